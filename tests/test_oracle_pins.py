@@ -1,0 +1,505 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these tests retypes an oracle formula: each value is reached by a
+different route (exact polynomial integration, finite-difference Jacobians of
+the governing equations, invariants, limits, convergence orders, the exact
+Riemann solution), so that a dropped term, a wrong sign or index or a
+transposed operand in the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from numpy.polynomial import polynomial as npoly
+
+from oracle import oracle as orc
+from paper_1908_02464_gb300 import problems as P
+
+rng = np.random.default_rng(1234)
+
+# ---------------------------------------------------------------------------
+# scalar reconstruction: Eq. eq6, eq9-eq11, eq16-eq18 (unit spacing, x_j = 0)
+# ---------------------------------------------------------------------------
+
+STENCILS = {0: [0, 1], 1: [-1, 0], 2: [0, 1, 2], 3: [-2, -1, 0], "01": [-1, 0, 1],
+            5: [-2, -1, 0, 1, 2]}
+
+
+def _cellavg_poly(offsets, f):
+    """Polynomial p (numpy coefficients) whose averages over the unit cells
+    [m - 1/2, m + 1/2], m in offsets, equal f[m]."""
+    k = len(offsets)
+    A = np.zeros((k, k))
+    for r, m in enumerate(offsets):
+        for e in range(k):
+            # average of x^e over [m-1/2, m+1/2]
+            A[r, e] = ((m + 0.5) ** (e + 1) - (m - 0.5) ** (e + 1)) / (e + 1)
+    return np.linalg.solve(A, np.array([f[m] for m in offsets], dtype=np.float64))
+
+
+def _int_sq_deriv(coef, l):
+    d = npoly.polyder(coef, l) if l > 0 else coef
+    sq = npoly.polymul(d, d)
+    anti = npoly.polyint(sq)
+    return npoly.polyval(0.5, anti) - npoly.polyval(-0.5, anti)
+
+
+def _fdict(f5):
+    return {m: f5[m + 2] for m in range(-2, 3)}
+
+
+@pytest.mark.parametrize("trial", range(20))
+def test_candidate_fluxes_are_cell_average_interpolants(trial):
+    f5 = rng.normal(size=5)
+    _, det = orc.recon(f5, 0.3)
+    fd = _fdict(f5)
+    for k in range(4):
+        p = _cellavg_poly(STENCILS[k], fd)
+        assert det["q"][k] == pytest.approx(npoly.polyval(0.5, p), rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("trial", range(20))
+def test_smoothness_indicators_equal_eq9_integrals(trial):
+    f5 = rng.normal(size=5) * 10 ** rng.uniform(-2, 2)
+    _, det = orc.recon(f5, 0.3)
+    fd = _fdict(f5)
+    for k in range(4):
+        p = _cellavg_poly(STENCILS[k], fd)
+        r = len(STENCILS[k])
+        beta = sum(_int_sq_deriv(p, l) for l in range(1, r))
+        assert det["beta"][k] == pytest.approx(beta, rel=1e-10, abs=1e-12 * np.max(np.abs(f5)) ** 2)
+    # Eq. eq10: tau_5 = high-order part (l = 3, 4) of the full-stencil indicator
+    p5 = _cellavg_poly(STENCILS[5], fd)
+    tau = _int_sq_deriv(p5, 3) + _int_sq_deriv(p5, 4)
+    assert det["tau5"] == pytest.approx(tau, rel=1e-9, abs=1e-12 * np.max(np.abs(f5)) ** 2)
+
+
+@pytest.mark.parametrize("trial", range(20))
+def test_error_terms_equal_eq16_integrals(trial):
+    f5 = rng.normal(size=5)
+    _, det = orc.recon(f5, 0.7)
+    fd = _fdict(f5)
+    ref = {0: "01", 1: "01", 2: 2, 3: 3}
+    for k in range(4):
+        pk = _cellavg_poly(STENCILS[k], fd)
+        pr = _cellavg_poly(STENCILS[ref[k]], fd)
+        diff = npoly.polysub(pk, pr)
+        E = _int_sq_deriv(diff, 0)
+        assert det["E"][k] == pytest.approx(E, rel=1e-10, abs=1e-13)
+
+
+@pytest.mark.parametrize("deg", range(5))
+def test_linear_weights_exact_on_polynomials(deg):
+    """Sum d_k q_k is the fifth-order upwind flux: exact h(x_{j+1/2}) when
+    f_m are the cell averages of a polynomial h of degree <= 4 (Eq. eq2-eq4)."""
+    for _ in range(5):
+        h = rng.normal(size=deg + 1)
+        f5 = [npoly.polyval(m + 0.5, npoly.polyint(h)) - npoly.polyval(m - 0.5, npoly.polyint(h))
+              for m in range(-2, 3)]
+        r, _ = orc.recon(f5, 0.0, weights="linear")
+        assert r == pytest.approx(npoly.polyval(0.5, h), rel=1e-12, abs=1e-12)
+
+
+def test_each_candidate_exact_to_its_degree():
+    for k, offs in [(0, 1), (1, 1), (2, 2), (3, 2)]:
+        for deg in range(offs + 1):
+            h = rng.normal(size=deg + 1)
+            H = npoly.polyint(h)
+            f5 = [npoly.polyval(m + 0.5, H) - npoly.polyval(m - 0.5, H) for m in range(-2, 3)]
+            _, det = orc.recon(f5, 0.5)
+            assert det["q"][k] == pytest.approx(npoly.polyval(0.5, h), rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("weights", ["reg", "is", "wang", "linear"])
+def test_constant_data_gives_optimal_weights(weights):
+    r, det = orc.recon([2.5] * 5, 3.0, weights=weights)
+    assert r == pytest.approx(2.5, rel=1e-15)
+    assert np.allclose(det["omega"], [0.4, 0.2, 0.3, 0.1], rtol=0, atol=1e-15)
+
+
+def test_lambda_zero_gives_optimal_weights():
+    for _ in range(10):
+        _, det = orc.recon(rng.normal(size=5), 0.0)
+        assert np.allclose(det["omega"], [0.4, 0.2, 0.3, 0.1], rtol=0, atol=1e-15)
+
+
+def test_large_lambda_recovers_eq8_weights():
+    """lambda -> infinity removes E_k: Eq. eq8-r tends to Eq. eq8."""
+    for _ in range(10):
+        f5 = rng.normal(size=5)
+        _, dr = orc.recon(f5, 1e14)
+        _, di = orc.recon(f5, 0.0, weights="is")
+        assert np.allclose(dr["omega"], di["omega"], rtol=1e-10, atol=1e-14)
+
+
+def test_regularization_lowers_two_point_weights():
+    """Sec. 3.1-3.2: the L2 error term only penalizes the two-point stencils.
+    With lambda = 1 the three-point alphas equal those of Eq. eq8 while the
+    two-point ones shrink, so omega_{0,1} / omega_{2,3} strictly decreases."""
+    checked = 0
+    for _ in range(50):
+        f5 = rng.normal(size=5)
+        _, dr = orc.recon(f5, 1.0)
+        _, di = orc.recon(f5, 0.0, weights="is")
+        assert dr["alpha"][2] == pytest.approx(di["alpha"][2], rel=1e-14)
+        assert dr["alpha"][3] == pytest.approx(di["alpha"][3], rel=1e-14)
+        if dr["E"][0] > 1e-6 and dr["tau5"] > 1e-6:
+            for a in (0, 1):
+                for b in (2, 3):
+                    assert dr["omega"][a] / dr["omega"][b] < di["omega"][a] / di["omega"][b]
+            checked += 1
+    assert checked > 20
+
+
+def test_wang_beta01_is_s01_indicator():
+    """Eq. eq15: beta_01 is the Jiang-Shu indicator of S01; recovered from the
+    Wang weights alpha_0 / d_0 - 1 = tau5^2 / ((beta0 + eps)(beta01 + eps))."""
+    for _ in range(10):
+        f5 = rng.normal(size=5)
+        _, dw = orc.recon(f5, 0.0, weights="wang")
+        fd = _fdict(f5)
+        p01 = _cellavg_poly(STENCILS["01"], fd)
+        b01 = _int_sq_deriv(p01, 1) + _int_sq_deriv(p01, 2)
+        lhs = dw["alpha"][0] / 0.4 - 1.0
+        rhs = dw["tau5"] ** 2 / ((dw["beta"][0] + 1e-20) * (b01 + 1e-20))
+        assert lhs == pytest.approx(rhs, rel=1e-9)
+
+
+def test_weight_deviation_is_fourth_order():
+    """Eq. eq277 / Sec. 3.1: omega^r_k - d_k = O(dx^4) at non-critical points."""
+    x0 = 0.3
+    devs = []
+    hs = [0.08, 0.04, 0.02, 0.01]
+    for h in hs:
+        # f_m: cell averages of sin over cells of width h centred at x0 + m h
+        f5 = [(-math.cos(x0 + (m + 0.5) * h) + math.cos(x0 + (m - 0.5) * h)) / h for m in range(-2, 3)]
+        _, det = orc.recon(f5, 1.0)
+        devs.append(np.max(np.abs(det["omega"] - np.array([0.4, 0.2, 0.3, 0.1]))))
+    devs = np.array(devs)
+    slopes = np.log2(devs[:-1] / devs[1:])
+    assert np.all(slopes > 3.8), slopes
+
+
+# ---------------------------------------------------------------------------
+# eigensystem (Sec. 2.4 steps (1)-(2)): checked against the governing equations
+# ---------------------------------------------------------------------------
+
+def _phys_flux(U, d, dim, gamma):
+    """Flux of the Euler equations (Eq. goveq4 and its multi-D form)."""
+    rho = U[0]
+    u = U[1:1 + dim] / rho
+    E = U[1 + dim]
+    p = (gamma - 1) * (E - 0.5 * rho * np.dot(u, u))
+    F = np.zeros(dim + 2)
+    F[0] = U[1 + d]
+    F[1:1 + dim] = U[1:1 + dim] * u[d]
+    F[1 + d] += p
+    F[1 + dim] = (E + p) * u[d]
+    return F
+
+
+def _jac(U, d, dim, gamma):
+    n = dim + 2
+    J = np.zeros((n, n))
+    for k in range(n):
+        h = 1e-6 * max(1.0, abs(U[k]))
+        e = np.zeros(n); e[k] = h
+        J[:, k] = (_phys_flux(U + e, d, dim, gamma) - _phys_flux(U - e, d, dim, gamma)) / (2 * h)
+    return J
+
+
+def _rand_cons(dim):
+    rho = rng.uniform(0.2, 3.0)
+    u = rng.uniform(-2, 2, size=dim)
+    p = rng.uniform(0.2, 5.0)
+    return np.concatenate([[rho], rho * u, [p / 0.4 + 0.5 * rho * np.dot(u, u)]])
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_eigenvectors_inverse_and_diagonalize_roe_jacobian(dim):
+    gamma = 1.4
+    prob = dict(dim=dim, n=[8] * dim, lo=[0] * dim, hi=[1] * dim, bc_lo=[0] * dim, bc_hi=[0] * dim)
+    for d in range(dim):
+        for _ in range(5):
+            UA, UB = _rand_cons(dim), _rand_cons(dim)
+            L, R, lam, rho_t = orc.roe_eigen(prob, d, UA, UB)
+            assert np.allclose(L @ R, np.eye(dim + 2), atol=1e-12)
+            # the Roe state read back from the eigenvectors
+            u_t = R[1:1 + dim, 1]
+            H_t = 0.5 * (R[dim + 1, 0] + R[dim + 1, dim + 1])
+            rho0 = 1.0
+            p0 = (gamma - 1) / gamma * rho0 * (H_t - 0.5 * np.dot(u_t, u_t))
+            U_roe = np.concatenate([[rho0], rho0 * u_t, [p0 / (gamma - 1) + 0.5 * rho0 * np.dot(u_t, u_t)]])
+            A = _jac(U_roe, d, dim, gamma)
+            assert np.allclose(R @ np.diag(lam) @ L, A, rtol=1e-6, atol=1e-6)
+            # Roe property: A(U_roe) (U_B - U_A) = F(U_B) - F(U_A)
+            dF = _phys_flux(UB, d, dim, gamma) - _phys_flux(UA, d, dim, gamma)
+            assert np.allclose(A @ (UB - UA), dF, rtol=1e-6, atol=1e-6)
+            assert rho_t == pytest.approx(math.sqrt(UA[0] * UB[0]), rel=1e-14)
+            # eigenvalues: normal velocity -+ sound speed
+            c_t = 0.5 * (lam[-1] - lam[0])
+            assert c_t ** 2 == pytest.approx((gamma - 1) * (H_t - 0.5 * np.dot(u_t, u_t)), rel=1e-12)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_cell_flux_matches_governing_equations(dim):
+    prob = dict(dim=dim, n=[8] * dim, lo=[0] * dim, hi=[1] * dim, bc_lo=[0] * dim, bc_hi=[0] * dim)
+    for d in range(dim):
+        U = _rand_cons(dim)
+        F, lam = orc.cell_flux(prob, d, U)
+        assert np.allclose(F, _phys_flux(U, d, dim, 1.4), rtol=1e-14, atol=1e-14)
+        ev = np.sort(np.linalg.eigvals(_jac(U, d, dim, 1.4)).real)
+        assert np.allclose(np.sort(lam), ev, rtol=1e-6, atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# face flux: hybrid, detector, splitting (Sec. 2.4, 3.2, 3.3)
+# ---------------------------------------------------------------------------
+
+def _random_six(dim, smooth=False):
+    if smooth:
+        base = _rand_cons(dim)
+        slope = 0.01 * _rand_cons(dim)
+        return np.stack([base + slope * m for m in range(6)])
+    return np.stack([_rand_cons(dim) for _ in range(6)])
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_linear_upwind_equals_weno_with_optimal_weights(dim):
+    """Eq. linearupwind (with the 1/60 of Eq. eq28) is the characteristic WENO
+    flux with omega_k = d_k; both are computed by different oracle paths."""
+    base = dict(dim=dim, n=[8] * dim, lo=[0] * dim, hi=[1] * dim, bc_lo=[0] * dim, bc_hi=[0] * dim)
+    for d in range(dim):
+        for _ in range(5):
+            U6 = _random_six(dim)
+            ups = dict(base, hybrid=1)
+            lin = dict(base, hybrid=0, weights="linear")
+            F1, s1, _ = orc.face_flux(ups, d, U6, eps_h=1e300)
+            F2, s2, _ = orc.face_flux(lin, d, U6)
+            assert s1 and not s2
+            assert np.allclose(F1, F2, rtol=1e-12, atol=1e-12 * np.max(np.abs(F2)))
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_constant_state_face_flux_is_physical_flux(dim):
+    base = dict(dim=dim, n=[8] * dim, lo=[0] * dim, hi=[1] * dim, bc_lo=[0] * dim, bc_hi=[0] * dim)
+    U = _rand_cons(dim)
+    U6 = np.stack([U] * 6)
+    for hybrid in (0, 1):
+        for d in range(dim):
+            F, smooth, sig = orc.face_flux(dict(base, hybrid=hybrid), d, U6)
+            assert np.allclose(F, _phys_flux(U, d, dim, 1.4), rtol=1e-13, atol=1e-13)
+            assert np.max(sig) < 1e-25
+            assert smooth == bool(hybrid)
+
+
+def test_detector_vanishes_on_quartic_data():
+    """Eq. eq28 is a fifth difference: zero on componentwise polynomials of
+    degree <= 4 and nonzero on degree 5."""
+    prob = dict(dim=1, n=[8], lo=[0], hi=[1], bc_lo=[0], bc_hi=[0])
+    base = np.array([1.0, 0.3, 2.5])
+    for deg in range(5):
+        c = rng.uniform(-0.02, 0.02, size=(deg + 1, 3))
+        U6 = np.stack([base + sum(c[e] * m ** e for e in range(deg + 1)) for m in range(6)])
+        _, _, sig = orc.face_flux(prob, 0, U6)
+        assert np.max(sig) < 1e-26
+    c5 = np.array([1e-4, 0, 0])
+    U6 = np.stack([base + c5 * m ** 5 for m in range(6)])
+    _, _, sig = orc.face_flux(prob, 0, U6)
+    assert np.max(sig) > 1e-12
+
+
+def test_detector_mirror_invariant():
+    """Reversing the six cells and the normal velocity changes the sign of dv
+    only: sigma per acoustic pair is swapped, the set of values is equal."""
+    prob = dict(dim=1, n=[8], lo=[0], hi=[1], bc_lo=[0], bc_hi=[0])
+    for _ in range(10):
+        U6 = _random_six(1)
+        M = U6[::-1].copy()
+        M[:, 1] *= -1
+        _, _, s1 = orc.face_flux(prob, 0, U6)
+        _, _, s2 = orc.face_flux(prob, 0, M)
+        assert np.allclose(np.sort(s1), np.sort(s2), rtol=1e-12)
+        assert s1[0] == pytest.approx(s2[2], rel=1e-12)
+
+
+def test_face_flux_mirror_antisymmetry():
+    """Mirror symmetry of the reconstruction (Sec. 2.4 step (5)): mirroring the
+    stencil negates the mass and energy flux and keeps the momentum flux."""
+    for hybrid in (0, 1):
+        prob = dict(dim=1, n=[8], lo=[0], hi=[1], bc_lo=[0], bc_hi=[0], hybrid=hybrid)
+        for _ in range(10):
+            U6 = _random_six(1)
+            M = U6[::-1].copy()
+            M[:, 1] *= -1
+            F1, _, _ = orc.face_flux(prob, 0, U6)
+            F2, _, _ = orc.face_flux(prob, 0, M)
+            assert np.allclose(F1 * np.array([-1, 1, -1]), F2, rtol=1e-12, atol=1e-12)
+
+
+def test_hybrid_flags_follow_discontinuities():
+    """Sec. 3.3: smooth region -> linear scheme, faces near a shock -> WENO."""
+    prob, U = P.shu_osher(400)
+    _, flags, ratio = orc.rhs(prob, U, 0.0, want_flags=True)
+    # the jump sits at face 40 (between cells 39 and 40); face i uses cells
+    # i-3 .. i+2, so faces 38..42 see it
+    near = np.abs(np.arange(401) - 40) <= 2
+    assert np.all(flags[near] == 0)
+    far = np.abs(np.arange(401) - 40) > 6
+    assert np.mean(flags[far]) > 0.9
+    assert np.all((ratio < 1.0) == (flags == 1))
+
+
+# ---------------------------------------------------------------------------
+# semi-discrete operator: conservation, symmetry, consistency (Eq. goveq5)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,n", [(1, [64]), (2, [24, 16]), (3, [12, 10, 8])])
+@pytest.mark.parametrize("kind", ["smooth", "mixed", "jumps"])
+def test_conservation_periodic(dim, n, kind):
+    prob, U = P.random_state(dim, n, seed=7 + dim, kind=kind)
+    dU = orc.rhs(prob, U)
+    dV = np.prod([1.0 / m for m in n])
+    tot = dU.reshape(dim + 2, -1).sum(axis=1) * dV
+    scale = np.max(np.abs(dU), axis=tuple(range(1, dim + 1))) * dV * U[0].size
+    assert np.all(np.abs(tot) <= 1e-13 * scale)
+
+
+def test_conservation_telescopes_to_boundary_flux():
+    """Transmissive Sod at t = 0: the sum of dU dx equals the difference of the
+    boundary fluxes, which are the physical fluxes of the constant end states."""
+    prob, U = P.sod(200)
+    dU = orc.rhs(prob, U)
+    dx = 1.0 / 200
+    lhs = dU.sum(axis=1) * dx
+    rhs = -(_phys_flux(U[:, -1], 0, 1, 1.4) - _phys_flux(U[:, 0], 0, 1, 1.4))
+    assert np.allclose(lhs, rhs, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_constant_state_rhs_zero(dim):
+    n = [10, 8, 6][:dim]
+    prob, _ = P.random_state(dim, n, seed=3)
+    U = np.zeros((dim + 2,) + tuple(reversed(n)))
+    Uc = _rand_cons(dim)
+    for v in range(dim + 2):
+        U[v] = Uc[v]
+    dU = orc.rhs(prob, U)
+    assert np.max(np.abs(dU)) < 1e-11 * np.max(np.abs(Uc)) * 10
+
+
+def test_mirror_symmetry_of_solution():
+    """Symmetric data rho(x) = rho(1-x), u(x) = -u(1-x), p(x) = p(1-x) stay
+    symmetric (Sec. 2.4: mirror-symmetric reconstruction)."""
+    n = 200
+    x = P.centers(0, 1, n)
+    mid = np.abs(x - 0.5) < 0.2
+    rho = np.where(mid, 1.0, 0.125)
+    p = np.where(mid, 1.0, 0.1)
+    u = np.zeros(n)
+    U = P.prim_to_cons(1.4, rho, [u], p)
+    prob, _ = P.sod(n)
+    st, t, k = orc.advance(prob, U, 0.0, 0.1)
+    assert st == 0 and k > 10
+    assert np.allclose(U[0], U[0][::-1], rtol=1e-12, atol=1e-13)
+    assert np.allclose(U[1], -U[1][::-1], rtol=1e-12, atol=1e-13)
+    assert np.allclose(U[2], U[2][::-1], rtol=1e-12, atol=1e-13)
+
+
+def test_totals_conserved_in_time_periodic():
+    prob, U = P.random_state(2, [32, 24], seed=11, kind="mixed")
+    t0 = orc.totals(prob, U)
+    st, t, k = orc.advance(prob, U, 0.0, 1.0, max_steps=5)
+    assert st == 0 and k == 5
+    assert np.allclose(orc.totals(prob, U), t0, rtol=1e-13, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# exact Riemann solver (used as a reference) and shock tubes (Sec. 4.2)
+# ---------------------------------------------------------------------------
+
+def test_exact_riemann_jump_conditions():
+    """Sod: left rarefaction, right shock.  Rankine-Hugoniot across the shock,
+    isentropy and the Riemann invariant across the fan, p and u continuous at
+    the contact."""
+    g = 1.4
+    WL, WR = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    vac, ps, us = orc.riemann_star(g, WL, WR)
+    assert not vac
+    t = 0.2
+    xs = np.linspace(0.0, 1.0, 20001)
+    W = orc.riemann_sample(g, WL, WR, 0.5, t, xs)
+    # shock position: last change of state at the right
+    i = np.max(np.nonzero(np.abs(W[0] - WR[0]) > 1e-12)[0])
+    S = (xs[i] - 0.5) / t
+    rs, uss = W[0, i - 1], W[1, i - 1]
+    assert uss == pytest.approx(us, rel=1e-12)
+    # mass and momentum fluxes through the moving shock
+    m1 = WR[0] * (WR[1] - S); m2 = rs * (us - S)
+    assert m1 == pytest.approx(m2, rel=2e-3)
+    M1 = WR[0] * WR[1] * (WR[1] - S) + WR[2]; M2 = rs * us * (us - S) + ps
+    assert M1 == pytest.approx(M2, rel=2e-3)
+    # isentropic left wave and constant invariant u + 2c/(g-1)
+    fan = (W[2] < WL[2] - 1e-9) & (W[2] > ps + 1e-9)
+    assert fan.sum() > 100
+    s = W[2][fan] / W[0][fan] ** g
+    assert np.allclose(s, WL[2] / WL[0] ** g, rtol=1e-12)
+    c = np.sqrt(g * W[2][fan] / W[0][fan])
+    assert np.allclose(W[1][fan] + 2 * c / (g - 1), 2 * math.sqrt(g) / (g - 1), rtol=1e-12)
+
+
+def test_exact_riemann_symmetric_123():
+    vac, ps, us = orc.riemann_star(1.4, (1.0, -2.0, 0.4), (1.0, 2.0, 0.4))
+    assert not vac and abs(us) < 1e-12 and 0 < ps < 0.4
+    vac, _, _ = orc.riemann_star(1.4, (1.0, -20.0, 0.4), (1.0, 20.0, 0.4))
+    assert vac
+
+
+def test_sod_converges_to_exact_solution():
+    errs = []
+    for n in (100, 200, 400):
+        prob, U = P.sod(n)
+        st, t, k = orc.advance(prob, U, 0.0, prob["t_end"])
+        assert st == 0 and t == pytest.approx(0.2)
+        W = orc.riemann_sample(1.4, prob["WL"], prob["WR"], 0.5, 0.2, P.centers(0, 1, n))
+        errs.append(np.mean(np.abs(U[0] - W[0])))
+    assert errs[1] < 5e-3
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_lax_and_123_run_and_track_exact():
+    for fn, tol in ((P.lax, 2e-2), (P.problem_123, 2e-2)):
+        prob, U = fn(200)
+        st, t, k = orc.advance(prob, U, 0.0, prob["t_end"])
+        assert st == 0
+        W = orc.riemann_sample(1.4, prob["WL"], prob["WR"], 0.5, prob["t_end"], P.centers(0, 1, 200))
+        assert np.mean(np.abs(U[0] - W[0])) < tol
+
+
+# ---------------------------------------------------------------------------
+# formal order on smooth periodic data (configs: sin(pi x), N = 20..640)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["advection", "density_wave"])
+def test_fifth_order_convergence(which):
+    fn = P.advection_sine if which == "advection" else P.density_wave
+    errs = []
+    ns = [20, 40, 80, 160]
+    for n in ns:
+        prob, U = fn(n)
+        st, t, k = orc.advance(prob, U, 0.0, prob["t_end"])
+        assert st == 0
+        x = P.centers(-1, 1, n)
+        ex = np.sin(np.pi * (x - 0.5)) if which == "advection" else 1 + 0.2 * np.sin(np.pi * (x - 0.5))
+        errs.append(np.mean(np.abs(U[0] - ex)))
+    order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(order[1:] > 4.7), order
+
+
+def test_nonphysical_state_reported_and_restored():
+    prob, U = P.sod(50)
+    U[2, 10] = -1.0   # negative energy -> negative pressure
+    U0 = U.copy()
+    st, t, dt = orc.step(prob, U, 0.0, 1.0)
+    assert st == 3
+    assert np.array_equal(U, U0)
