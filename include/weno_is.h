@@ -1,0 +1,192 @@
+/*
+ * weno_is.h -- C ABI of the GB300 (sm_103a) library for the L2-norm
+ * regularized incremental-stencil WENO scheme of Zhu & Hu (arXiv 1908.02464)
+ * applied to the compressible Euler equations.
+ *
+ * The library computes, on one GPU, the semi-discrete right-hand side
+ *     dU_j/dt = - sum_d (F^_{j+1/2} - F^_{j-1/2}) / dx_d          (Eq. goveq5)
+ * with the characteristic-wise numerical flux of Sec. 2.4 (Roe average,
+ * eigensystem, projection Eq. eqchara, local Lax-Friedrichs splitting
+ * Eq. flxuspliting, reconstruction Eq. reconstruction/reconstruction1,
+ * back-projection Eq. reconstruction2), the regularized weights Eq. eq8-r
+ * with the L2 error terms Eq. eq18, the detector and regularization
+ * parameter Eq. eq27-29 and the hybrid switch to the optimal linear upwind
+ * scheme Eq. eqhy/linearupwind/eq31; and advances it with the third-order
+ * TVD Runge-Kutta scheme at a CFL-limited time step (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a weno_status; nothing aborts or throws across the
+ *     ABI.  Errors raised on the device (non-physical state) are latched in a
+ *     status word and reported by the next call that synchronizes.
+ *   - State arrays are structure-of-arrays, interior cells only, C order
+ *     [nvar][nz][ny][nx] (nvar = dim + 2: rho, rho*u_x, [rho*u_y], [rho*u_z],
+ *     E).  The element type is double for WENO_FP64 and float for WENO_FP32
+ *     and WENO_MIXED.
+ *   - Pointers passed in are borrowed; the library copies what it keeps.
+ *     Device pointers must be allocated on the context's device and be
+ *     naturally aligned.
+ *   - All device work is issued on the stream given to weno_create (the
+ *     legacy default stream when NULL).  A context is not thread-safe.
+ */
+#ifndef WENO_IS_H
+#define WENO_IS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WENO_OK = 0,
+    WENO_ERR_INVALID_ARG = 1,   /* bad pointer, size, code or combination      */
+    WENO_ERR_CUDA = 2,          /* a CUDA runtime call failed (see last_error) */
+    WENO_ERR_NONPHYSICAL = 3,   /* rho <= 0, p <= 0 or a non-finite value      */
+    WENO_ERR_TIMEOUT = 4,       /* a bounded device wait ran out               */
+    WENO_ERR_UNSUPPORTED = 5    /* valid request that this build does not do   */
+} weno_status;
+
+typedef enum {
+    WENO_FP64 = 0,   /* all arithmetic and storage in double                    */
+    WENO_FP32 = 1,   /* float storage and arithmetic; time step, time and the
+                        conserved totals in double                             */
+    WENO_MIXED = 2   /* float storage and bulk arithmetic; the detector and the
+                        hybrid switch (Eq. eq27-28, eq31) in double             */
+} weno_precision;
+
+/* boundary codes, one per side and direction (ghost cells, three layers) */
+enum {
+    WENO_BC_TRANSMISSIVE = 0, /* copy of the nearest interior cell                    */
+    WENO_BC_REFLECT = 1,      /* mirror image, normal momentum negated                */
+    WENO_BC_PERIODIC = 2,     /* wrap-around                                          */
+    WENO_BC_INFLOW = 3,       /* fixed conservative state bc_state[0]                 */
+    WENO_BC_DMR_BOTTOM = 4,   /* y-low of the double Mach reflection (Sec. 4.5):
+                                 bc_state[0] for x < 1/6, reflecting wall otherwise */
+    WENO_BC_DMR_TOP = 5       /* y-high of the double Mach reflection: bc_state[0]
+                                 for x < 1/6 + (1 + 20 t)/sqrt(3), bc_state[1] else */
+};
+
+/* Uniform cell-centred grid x_i = lo + (i + 1/2) dx (Sec. 2.1, x_j = j dx). */
+typedef struct {
+    int dim;                 /* 1, 2 or 3                                    */
+    int n[3];                /* interior cells per direction (unused = 1)    */
+    double lo[3], hi[3];     /* domain bounds                                */
+    int bc_lo[3], bc_hi[3];  /* WENO_BC_* per side                           */
+    double bc_state[2][5];   /* conservative states used by INFLOW and DMR   */
+} weno_grid;
+
+/* Constants of the method.  Defaults (weno_default_params) are the paper's:
+ * gamma 1.4, CFL 0.5 (Sec. 4), eps 1e-20 (Eq. eq8), c 1 (Eq. eq29),
+ * C 1 and alpha 3 (Eq. eq31), L 1 (characteristic length of Eq. eq31). */
+typedef struct {
+    double gamma;
+    double cfl;
+    double eps;        /* epsilon of Eq. eq8-r                                  */
+    double c_lambda;   /* c of Eq. eq29: lambda = c sigma^s                      */
+    double C_thr;      /* C of Eq. eq31                                          */
+    double L_char;     /* L of Eq. eq31                                          */
+    int alpha_thr;     /* alpha of Eq. eq31 (integer power)                      */
+    int hybrid;        /* 1: linear upwind scheme where sigma^s < eps_h for all s */
+    int precision;     /* weno_precision                                         */
+} weno_params;
+
+typedef struct weno_ctx weno_ctx;
+
+/* Fill *p with the paper's constants and WENO_FP64. */
+weno_status weno_default_params(weno_params* p);
+
+/* Create a context on the current CUDA device.  Allocates the state buffers
+ * (three rotating RK states and, for dim >= 2, one RHS accumulator, each with
+ * three ghost layers), the device scalars and the reduction scratch.
+ * stream: a cudaStream_t cast to void* (NULL = legacy default stream).
+ * Errors: WENO_ERR_INVALID_ARG for dim outside 1..3, n < 1, a domain with
+ * hi <= lo, an unknown BC code, a periodic side paired with a non-periodic
+ * one, n < 3 in a periodic direction, or an unknown precision;
+ * WENO_ERR_CUDA when allocation fails.  On error *out is NULL. */
+weno_status weno_create(const weno_grid* grid, const weno_params* params, void* stream,
+                        weno_ctx** out);
+
+/* Release every device allocation of the context; NULL is accepted. */
+void weno_destroy(weno_ctx* ctx);
+
+/* Copy a state into the context and set the time to t (steps counter and
+ * device status are reset).  U: interior-only array (see conventions), host
+ * memory when on_device = 0, device memory otherwise. */
+weno_status weno_set_state(weno_ctx* ctx, const void* U, int on_device, double t);
+
+/* Copy the current state out (same layout) and, if t is not NULL, the time.
+ * Synchronizes the context's stream. */
+weno_status weno_get_state(weno_ctx* ctx, void* U, int on_device, double* t);
+
+/* Semi-discrete right-hand side dU/dt (Eq. goveq5 summed over directions) of
+ * the interior-only device array U_dev, with ghost cells filled at time t.
+ * dUdt_dev: interior-only device array of the same shape, overwritten.  The
+ * context's own state is not touched.  Asynchronous on the context's
+ * stream; returns WENO_ERR_CUDA if a launch fails. */
+weno_status weno_rhs(weno_ctx* ctx, const void* U_dev, void* dUdt_dev, double t);
+
+/* Per-face hybrid flags of U_dev at time t: 1 where the linear upwind scheme
+ * is used (Eq. eqhy, sigma_{j+1/2} = 1), 0 where the regularized WENO-IS flux
+ * is used.  flags_dev: uint8 device array holding, for each direction d in
+ * order, the faces of shape [nz][ny][nx] with n_d + 1 entries along d (face
+ * i - 1/2 lies between cells i - 1 and i).  Asynchronous. */
+weno_status weno_face_flags(weno_ctx* ctx, const void* U_dev, double t, uint8_t* flags_dev);
+
+/* One TVD RK3 step of the context's state.  dt = CFL / max_cells
+ * sum_d (|u_d| + c) / dx_d, clipped so that t + dt <= t_end (time reaches
+ * t_end exactly on the clipped step).  Writes the dt taken (0 when t >= t_end)
+ * to *dt_taken if not NULL.  Synchronizes.  On a non-physical stage state
+ * returns WENO_ERR_NONPHYSICAL and leaves state and time at the last good
+ * step. */
+weno_status weno_step(weno_ctx* ctx, double t_end, double* dt_taken);
+
+/* Up to max_steps steps towards t_end, replayed from CUDA graphs in chunks
+ * (the host reads the device time and status once per chunk).  *steps_taken
+ * receives the number of completed steps.  Errors as weno_step. */
+weno_status weno_advance(weno_ctx* ctx, double t_end, int max_steps, int* steps_taken);
+
+/* Asynchronous stepping: enqueue nsteps RK3 steps (CUDA-graph replays)
+ * towards t_end on the context's stream and return without synchronizing.
+ * Steps that would pass t_end, and every step after a non-physical stage,
+ * do nothing on the device; the next synchronizing call (weno_get_time,
+ * weno_get_state, weno_step, ...) reads the true time, step count and
+ * status.  Errors: WENO_ERR_CUDA if capture or a launch fails. */
+weno_status weno_enqueue_steps(weno_ctx* ctx, double t_end, int nsteps);
+
+/* Measurement helper (no counterpart in the paper): times `reps` launches of
+ * the sweep kernel of every direction on the current state (ghosts filled at
+ * the current time; the sweeps write the RHS accumulator only, the state is
+ * not changed), each launch bracketed by CUDA events on the context's stream.
+ * If flush_dev is not NULL, flush_bytes of it are overwritten before every
+ * launch (to evict L2).  ms[d] receives the mean launch time of direction d,
+ * weno_faces[d] (if not NULL) the number of faces of one launch that took
+ * the WENO flux.  Synchronizes. */
+weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t flush_bytes, double* ms,
+                             unsigned long long* weno_faces);
+
+/* Conserved totals sum_cells U dV per variable (nvar doubles, host memory),
+ * accumulated in double.  Synchronizes. */
+weno_status weno_conserved_totals(weno_ctx* ctx, double* totals);
+
+/* Number of faces computed with the WENO (non-linear) flux since the last
+ * call with reset != 0, over every sweep launched by weno_rhs, weno_step
+ * and weno_advance.  Synchronizes. */
+weno_status weno_weno_face_count(weno_ctx* ctx, unsigned long long* count, int reset);
+
+/* Time and completed steps of the context (host copies; synchronizes). */
+weno_status weno_get_time(weno_ctx* ctx, double* t, long long* steps);
+
+/* Human-readable text of the last error of ctx (or of the last failed
+ * weno_create when ctx is NULL).  Valid until the next call on ctx. */
+const char* weno_last_error(const weno_ctx* ctx);
+
+/* Measurement helper (no counterpart in the paper): peak fused multiply-add
+ * throughput of the current device in FLOP/s for precision 0 = double,
+ * 1 = float, from a dependent-chain kernel that fills every SM.  Writes the
+ * rate to *flops and the kernel time in seconds to *seconds.  Synchronizes. */
+weno_status weno_measure_fma_peak(int precision, double* flops, double* seconds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WENO_IS_H */

@@ -653,7 +653,9 @@ static int rk3_step(Grid& G, double& t, double t_end, double* dt_out)
     const int nv = G.nv;
     const size_t ni = G.interior_size();
     double dt = cfl_dt(G);
-    if (t + dt > t_end) dt = t_end - t;
+    /* the step that reaches t_end is clipped and ends exactly at t_end */
+    const bool last = (t + dt >= t_end);
+    if (last) dt = t_end - t;
     if (!(dt > 0.0)) { if (dt_out) *dt_out = 0.0; return 0; }
 
     std::vector<double> U0(nv * ni), Ut(nv * ni), L;
@@ -672,7 +674,7 @@ static int rk3_step(Grid& G, double& t, double t_end, double* dt_out)
     G.load_interior(Ut.data());
 
     if (!state_ok(G)) { G.load_interior(U0.data()); return 3; }
-    t += dt;
+    t = last ? t_end : t + dt;
     if (dt_out) *dt_out = dt;
     return 0;
 }

@@ -1,0 +1,682 @@
+// Host side of the C ABI declared in include/weno_is.h: context, buffers,
+// the RK3 step sequence and its CUDA-graph replay.
+//
+// Step sequence (one RK3 step, Sec. 4 of the paper) on three rotating state
+// buffers (cur, x, y) selected by phase = completed steps mod 3:
+//   k_cfl(cur) -> k_dt
+//   stage 1: ghosts(cur, t)        sweeps(cur)         -> x = cur + dt L(cur)
+//   stage 2: ghosts(x, t+dt)       sweeps(x), base cur -> y = 3/4 cur + 1/4 (x + dt L(x))
+//   stage 3: ghosts(y, t+dt/2)     sweeps(y), base cur -> x = 1/3 cur + 2/3 (y + dt L(y))
+//   k_post (t += dt, steps += 1 unless a stage failed)
+// The new state is x, i.e. buffer (phase + 1) mod 3.  A failed admissibility
+// check latches the device status; later kernels of the step do nothing, the
+// step is not counted and the state stays in cur.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/weno_is.h"
+#include "weno_launch.cuh"
+
+using wis::DevTime;
+
+struct weno_ctx {
+    weno_grid g;
+    weno_params p;
+    int dim = 1, nv = 3, prec = 0, dev = 0, nsm = 1;
+    size_t esz = 8;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    int n[3] = {1, 1, 1};
+    int N[3] = {1, 1, 1};
+    long long sy = 0, sz = 0, sv = 0, off0 = 0;
+    size_t buf_elems = 0;
+    double dx[3] = {1, 1, 1}, inv_dx[3] = {1, 1, 1}, eps_h[3] = {0, 0, 0};
+    void* buf[3] = {nullptr, nullptr, nullptr};
+    void* acc = nullptr;
+    void* rhs_in = nullptr;
+    void* rhs_out = nullptr;
+    void* stage_io = nullptr;   // interior-size staging for host copies
+    DevTime* tm = nullptr;
+    DevTime* tm_host = nullptr; // pinned
+    unsigned long long* wcount = nullptr;
+    double* partial = nullptr;
+    double* totals_dev = nullptr;
+    int tot_blocks = 1;
+    int phase = 0;
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    bool graphs_ready = false;
+    std::string err;
+};
+
+static std::string g_create_err;
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            return WENO_ERR_CUDA;                                                           \
+        }                                                                                   \
+    } while (0)
+
+static size_t interior_cells(const weno_ctx* c) { return (size_t)c->n[0] * c->n[1] * c->n[2]; }
+
+// ----------------------------------------------------------- dispatch
+static cudaError_t do_sweep(weno_ctx* c, int dir, const wis::SweepArgs& a, cudaStream_t s)
+{
+    if (c->prec == WENO_FP64) return wis::sweep_f64(c->dim, dir, a, s);
+    if (c->prec == WENO_FP32) return wis::sweep_f32(c->dim, dir, a, s);
+    return wis::sweep_mixed(c->dim, dir, a, s);
+}
+static cudaError_t do_ghost(weno_ctx* c, const wis::GhostArgs& a, cudaStream_t s)
+{
+    return c->prec == WENO_FP64 ? wis::ghost_f64(c->dim, a, s) : wis::ghost_f32(c->dim, a, s);
+}
+static cudaError_t do_cfl(weno_ctx* c, const wis::CflArgs& a, cudaStream_t s)
+{
+    return c->prec == WENO_FP64 ? wis::cfl_f64(c->dim, a, c->nsm, s) : wis::cfl_f32(c->dim, a, c->nsm, s);
+}
+static cudaError_t do_pack(weno_ctx* c, const void* src, void* dst, int to_ghosted, cudaStream_t s)
+{
+    if (c->prec == WENO_FP64)
+        return wis::pack_f64(src, dst, c->nv, c->n, c->sy, c->sz, c->sv, c->off0, to_ghosted, c->nsm, s);
+    return wis::pack_f32(src, dst, c->nv, c->n, c->sy, c->sz, c->sv, c->off0, to_ghosted, c->nsm, s);
+}
+
+static wis::SweepArgs sweep_args(weno_ctx* c, int dir)
+{
+    wis::SweepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int k = 0; k < 3; ++k) a.n[k] = c->n[k];
+    a.sy = c->sy; a.sz = c->sz; a.sv = c->sv; a.off0 = c->off0;
+    a.inv_dx = c->inv_dx[dir];
+    a.eps_h = c->eps_h[dir];
+    a.gamma = c->p.gamma;
+    a.eps = c->p.eps;
+    a.c_lambda = c->p.c_lambda;
+    a.hybrid = c->p.hybrid;
+    a.weno_count = c->wcount;
+    return a;
+}
+
+static wis::GhostArgs ghost_args(weno_ctx* c, void* U, int dir)
+{
+    wis::GhostArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.U = U;
+    a.dir = dir;
+    for (int k = 0; k < 3; ++k) a.n[k] = c->n[k];
+    a.sy = c->sy; a.sz = c->sz; a.sv = c->sv; a.off0 = c->off0;
+    a.bc_lo = c->g.bc_lo[dir];
+    a.bc_hi = c->g.bc_hi[dir];
+    for (int s = 0; s < 2; ++s)
+        for (int v = 0; v < 5; ++v) a.bc_state[s][v] = c->g.bc_state[s][v];
+    a.lo0 = c->g.lo[0];
+    a.dx0 = c->dx[0];
+    return a;
+}
+
+// one RK stage: ghosts of `in` at the stage time, then the sweeps
+static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* out, double ra, double rb,
+                               double stage_c, cudaStream_t s)
+{
+    for (int d = 0; d < c->dim; ++d) {
+        wis::GhostArgs ga = ghost_args(c, in, d);
+        ga.tm = c->tm;
+        ga.stage_c = stage_c;
+        cudaError_t e = do_ghost(c, ga, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (int d = 0; d < c->dim; ++d) {
+        wis::SweepArgs a = sweep_args(c, d);
+        a.U = in;
+        a.tm = c->tm;
+        if (d == c->dim - 1) {
+            a.mode = wis::MODE_COMBINE;
+            a.Un = base;
+            a.out = out;
+            a.acc = c->dim > 1 ? c->acc : nullptr;
+            a.rk_a = ra;
+            a.rk_b = rb;
+        } else {
+            a.mode = d == 0 ? wis::MODE_ACC_SET : wis::MODE_ACC_ADD;
+            a.acc = c->acc;
+        }
+        cudaError_t e = do_sweep(c, d, a, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+static cudaError_t issue_step(weno_ctx* c, int ph, cudaStream_t s)
+{
+    void* cur = c->buf[ph % 3];
+    void* x = c->buf[(ph + 1) % 3];
+    void* y = c->buf[(ph + 2) % 3];
+    wis::CflArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.U = cur;
+    for (int k = 0; k < 3; ++k) { ca.n[k] = c->n[k]; ca.inv_dx[k] = k < c->dim ? c->inv_dx[k] : 0.0; }
+    ca.sy = c->sy; ca.sz = c->sz; ca.sv = c->sv; ca.off0 = c->off0;
+    ca.gamma = c->p.gamma;
+    ca.tm = c->tm;
+    cudaError_t e = do_cfl(c, ca, s);
+    if (e != cudaSuccess) return e;
+    wis::k_dt<<<1, 1, 0, s>>>(c->tm, c->p.cfl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = issue_stage(c, cur, nullptr, x, 0.0, 1.0, 0.0, s)) != cudaSuccess) return e;
+    if ((e = issue_stage(c, x, cur, y, 0.75, 0.25, 1.0, s)) != cudaSuccess) return e;
+    if ((e = issue_stage(c, y, cur, x, 1.0 / 3.0, 2.0 / 3.0, 0.5, s)) != cudaSuccess) return e;
+    wis::k_post<<<1, 1, 0, s>>>(c->tm);
+    return cudaGetLastError();
+}
+
+static weno_status build_graphs(weno_ctx* ctx)
+{
+    if (ctx->graphs_ready) return WENO_OK;
+    for (int ph = 0; ph < 3; ++ph) {
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeRelaxed));
+        cudaError_t e = issue_step(ctx, ph, ctx->cap);
+        cudaError_t e2 = cudaStreamEndCapture(ctx->cap, &gr);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            ctx->err = std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+            return WENO_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&ctx->graph[ph], gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+            return WENO_ERR_CUDA;
+        }
+    }
+    ctx->graphs_ready = true;
+    return WENO_OK;
+}
+
+static weno_status read_time(weno_ctx* ctx)
+{
+    CK(cudaMemcpyAsync(ctx->tm_host, ctx->tm, sizeof(DevTime), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->phase = (int)(ctx->tm_host->steps % 3);
+    return WENO_OK;
+}
+
+// ----------------------------------------------------------- ABI
+extern "C" {
+
+weno_status weno_default_params(weno_params* p)
+{
+    if (!p) return WENO_ERR_INVALID_ARG;
+    p->gamma = 1.4;
+    p->cfl = 0.5;
+    p->eps = 1e-20;
+    p->c_lambda = 1.0;
+    p->C_thr = 1.0;
+    p->L_char = 1.0;
+    p->alpha_thr = 3;
+    p->hybrid = 1;
+    p->precision = WENO_FP64;
+    return WENO_OK;
+}
+
+static void free_all(weno_ctx* c)
+{
+    for (int k = 0; k < 3; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        if (c->buf[k]) cudaFree(c->buf[k]);
+    }
+    if (c->acc) cudaFree(c->acc);
+    if (c->rhs_in) cudaFree(c->rhs_in);
+    if (c->rhs_out) cudaFree(c->rhs_out);
+    if (c->stage_io) cudaFree(c->stage_io);
+    if (c->tm) cudaFree(c->tm);
+    if (c->tm_host) cudaFreeHost(c->tm_host);
+    if (c->wcount) cudaFree(c->wcount);
+    if (c->partial) cudaFree(c->partial);
+    if (c->totals_dev) cudaFree(c->totals_dev);
+    if (c->cap) cudaStreamDestroy(c->cap);
+}
+
+weno_status weno_create(const weno_grid* grid, const weno_params* params, void* stream, weno_ctx** out)
+{
+    if (out) *out = nullptr;
+    if (!grid || !params || !out) { g_create_err = "null argument"; return WENO_ERR_INVALID_ARG; }
+    const int dim = grid->dim;
+    if (dim < 1 || dim > 3) { g_create_err = "dim must be 1, 2 or 3"; return WENO_ERR_INVALID_ARG; }
+    if (params->precision < WENO_FP64 || params->precision > WENO_MIXED) {
+        g_create_err = "unknown precision";
+        return WENO_ERR_INVALID_ARG;
+    }
+    if (!(params->gamma > 1.0) || !(params->cfl > 0.0) || !(params->eps > 0.0) || params->alpha_thr < 0) {
+        g_create_err = "invalid method constants";
+        return WENO_ERR_INVALID_ARG;
+    }
+    for (int d = 0; d < dim; ++d) {
+        if (grid->n[d] < 3) { g_create_err = "n must be >= 3 in every direction"; return WENO_ERR_INVALID_ARG; }
+        if (!(grid->hi[d] > grid->lo[d])) { g_create_err = "hi must exceed lo"; return WENO_ERR_INVALID_ARG; }
+        for (int s = 0; s < 2; ++s) {
+            const int bc = s == 0 ? grid->bc_lo[d] : grid->bc_hi[d];
+            if (bc < WENO_BC_TRANSMISSIVE || bc > WENO_BC_DMR_TOP) {
+                g_create_err = "unknown boundary code";
+                return WENO_ERR_INVALID_ARG;
+            }
+        }
+        if ((grid->bc_lo[d] == WENO_BC_PERIODIC) != (grid->bc_hi[d] == WENO_BC_PERIODIC)) {
+            g_create_err = "periodic boundaries must be paired";
+            return WENO_ERR_INVALID_ARG;
+        }
+    }
+    weno_ctx* ctx = new (std::nothrow) weno_ctx();
+    if (!ctx) { g_create_err = "out of host memory"; return WENO_ERR_CUDA; }
+    ctx->g = *grid;
+    ctx->p = *params;
+    ctx->dim = dim;
+    ctx->nv = dim + 2;
+    ctx->prec = params->precision;
+    ctx->esz = ctx->prec == WENO_FP64 ? sizeof(double) : sizeof(float);
+    ctx->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&ctx->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->dev);
+    for (int d = 0; d < 3; ++d) {
+        ctx->n[d] = d < dim ? grid->n[d] : 1;
+        if (d < dim) {
+            ctx->dx[d] = (grid->hi[d] - grid->lo[d]) / grid->n[d];
+            ctx->inv_dx[d] = 1.0 / ctx->dx[d];
+            // Eq. eq31: eps_h = C (dx / L)^alpha
+            const double r = ctx->dx[d] / params->L_char;
+            double eh = params->C_thr;
+            for (int k = 0; k < params->alpha_thr; ++k) eh *= r;
+            ctx->eps_h[d] = eh;
+        }
+    }
+    // x: interior starts at element 32 so that rows of the interior are aligned
+    const int xoff = 32;
+    ctx->N[0] = ((xoff + ctx->n[0] + 3 + 31) / 32) * 32;
+    ctx->N[1] = dim >= 2 ? ctx->n[1] + 6 : 1;
+    ctx->N[2] = dim == 3 ? ctx->n[2] + 6 : 1;
+    ctx->sy = ctx->N[0];
+    ctx->sz = (long long)ctx->N[0] * ctx->N[1];
+    ctx->sv = ctx->sz * ctx->N[2];
+    ctx->off0 = xoff + (dim >= 2 ? 3 * ctx->sy : 0) + (dim == 3 ? 3 * ctx->sz : 0);
+    ctx->buf_elems = (size_t)ctx->sv * ctx->nv;
+    const size_t bytes = ctx->buf_elems * ctx->esz;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&ctx->buf[k], bytes);
+        if (e == cudaSuccess) e = cudaMemset(ctx->buf[k], 0, bytes);
+    }
+    if (e == cudaSuccess && dim > 1) {
+        e = cudaMalloc(&ctx->acc, bytes);
+        if (e == cudaSuccess) e = cudaMemset(ctx->acc, 0, bytes);
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->tm, sizeof(DevTime));
+    if (e == cudaSuccess) e = cudaMemset(ctx->tm, 0, sizeof(DevTime));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->tm_host, sizeof(DevTime));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->wcount, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(ctx->wcount, 0, sizeof(unsigned long long));
+    const long long cells = (long long)interior_cells(ctx);
+    ctx->tot_blocks = wis::grid_for(cells, 256, ctx->nsm * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->partial, sizeof(double) * ctx->tot_blocks * ctx->nv);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->totals_dev, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        g_create_err = std::string("weno_create: ") + cudaGetErrorString(e);
+        free_all(ctx);
+        delete ctx;
+        return WENO_ERR_CUDA;
+    }
+    std::memset(ctx->tm_host, 0, sizeof(DevTime));
+    *out = ctx;
+    return WENO_OK;
+}
+
+void weno_destroy(weno_ctx* ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+}
+
+const char* weno_last_error(const weno_ctx* ctx)
+{
+    if (!ctx) return g_create_err.c_str();
+    return ctx->err.c_str();
+}
+
+static weno_status ensure_stage_io(weno_ctx* ctx)
+{
+    if (!ctx->stage_io) CK(cudaMalloc(&ctx->stage_io, interior_cells(ctx) * ctx->nv * ctx->esz));
+    return WENO_OK;
+}
+
+weno_status weno_set_state(weno_ctx* ctx, const void* U, int on_device, double t)
+{
+    if (!ctx || !U) return WENO_ERR_INVALID_ARG;
+    const size_t bytes = interior_cells(ctx) * ctx->nv * ctx->esz;
+    const void* src = U;
+    if (!on_device) {
+        weno_status st = ensure_stage_io(ctx);
+        if (st != WENO_OK) return st;
+        CK(cudaMemcpyAsync(ctx->stage_io, U, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        src = ctx->stage_io;
+    }
+    CK(do_pack(ctx, src, ctx->buf[0], 1, ctx->stream));
+    std::memset(ctx->tm_host, 0, sizeof(DevTime));
+    ctx->tm_host->t = t;
+    ctx->tm_host->t_end = t;
+    CK(cudaMemcpyAsync(ctx->tm, ctx->tm_host, sizeof(DevTime), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->phase = 0;
+    return WENO_OK;
+}
+
+weno_status weno_get_state(weno_ctx* ctx, void* U, int on_device, double* t)
+{
+    if (!ctx || !U) return WENO_ERR_INVALID_ARG;
+    weno_status st = read_time(ctx);
+    if (st != WENO_OK) return st;
+    const size_t bytes = interior_cells(ctx) * ctx->nv * ctx->esz;
+    if (on_device) {
+        CK(do_pack(ctx, ctx->buf[ctx->phase], U, 0, ctx->stream));
+    } else {
+        st = ensure_stage_io(ctx);
+        if (st != WENO_OK) return st;
+        CK(do_pack(ctx, ctx->buf[ctx->phase], ctx->stage_io, 0, ctx->stream));
+        CK(cudaMemcpyAsync(U, ctx->stage_io, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (t) *t = ctx->tm_host->t;
+    return WENO_OK;
+}
+
+weno_status weno_get_time(weno_ctx* ctx, double* t, long long* steps)
+{
+    if (!ctx) return WENO_ERR_INVALID_ARG;
+    weno_status st = read_time(ctx);
+    if (st != WENO_OK) return st;
+    if (t) *t = ctx->tm_host->t;
+    if (steps) *steps = ctx->tm_host->steps;
+    return WENO_OK;
+}
+
+static weno_status ensure_rhs_bufs(weno_ctx* ctx)
+{
+    const size_t bytes = ctx->buf_elems * ctx->esz;
+    if (!ctx->rhs_in) {
+        CK(cudaMalloc(&ctx->rhs_in, bytes));
+        CK(cudaMemsetAsync(ctx->rhs_in, 0, bytes, ctx->stream));
+    }
+    if (!ctx->rhs_out) {
+        CK(cudaMalloc(&ctx->rhs_out, bytes));
+        CK(cudaMemsetAsync(ctx->rhs_out, 0, bytes, ctx->stream));
+    }
+    return WENO_OK;
+}
+
+// ghosts + sweeps of a stand-alone RHS on rhs_in -> rhs_out (flags optional)
+static weno_status issue_rhs(weno_ctx* ctx, double t, uint8_t* flags)
+{
+    for (int d = 0; d < ctx->dim; ++d) {
+        wis::GhostArgs ga = ghost_args(ctx, ctx->rhs_in, d);
+        ga.t_fixed = t;
+        CK(do_ghost(ctx, ga, ctx->stream));
+    }
+    long long foff = 0;
+    for (int d = 0; d < ctx->dim; ++d) {
+        wis::SweepArgs a = sweep_args(ctx, d);
+        a.U = ctx->rhs_in;
+        if (flags) a.flags = flags + foff;
+        if (d == ctx->dim - 1) {
+            a.mode = wis::MODE_RHS;
+            a.acc = ctx->dim > 1 ? ctx->acc : nullptr;
+            a.out = ctx->rhs_out;
+        } else {
+            a.mode = d == 0 ? wis::MODE_ACC_SET : wis::MODE_ACC_ADD;
+            a.acc = ctx->acc;
+        }
+        CK(do_sweep(ctx, d, a, ctx->stream));
+        long long nf = 1;
+        for (int k = 0; k < 3; ++k) nf *= (k == d) ? (long long)ctx->n[k] + 1 : ctx->n[k];
+        foff += nf;
+    }
+    return WENO_OK;
+}
+
+weno_status weno_rhs(weno_ctx* ctx, const void* U_dev, void* dUdt_dev, double t)
+{
+    if (!ctx || !U_dev || !dUdt_dev) return WENO_ERR_INVALID_ARG;
+    weno_status st = ensure_rhs_bufs(ctx);
+    if (st != WENO_OK) return st;
+    CK(do_pack(ctx, U_dev, ctx->rhs_in, 1, ctx->stream));
+    st = issue_rhs(ctx, t, nullptr);
+    if (st != WENO_OK) return st;
+    CK(do_pack(ctx, ctx->rhs_out, dUdt_dev, 0, ctx->stream));
+    return WENO_OK;
+}
+
+weno_status weno_face_flags(weno_ctx* ctx, const void* U_dev, double t, uint8_t* flags_dev)
+{
+    if (!ctx || !U_dev || !flags_dev) return WENO_ERR_INVALID_ARG;
+    weno_status st = ensure_rhs_bufs(ctx);
+    if (st != WENO_OK) return st;
+    CK(do_pack(ctx, U_dev, ctx->rhs_in, 1, ctx->stream));
+    return issue_rhs(ctx, t, flags_dev);
+}
+
+static weno_status finish_steps(weno_ctx* ctx)
+{
+    weno_status st = read_time(ctx);
+    if (st != WENO_OK) return st;
+    if (ctx->tm_host->status != 0) {
+        ctx->err = "non-physical state (rho <= 0, p <= 0 or non-finite) in a Runge-Kutta stage";
+        return WENO_ERR_NONPHYSICAL;
+    }
+    return WENO_OK;
+}
+
+static weno_status set_t_end(weno_ctx* ctx, double t_end)
+{
+    // tm_host is pinned; the copy is ordered before the step on the stream
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->tm_host->t_end = t_end;
+    CK(cudaMemcpyAsync(&ctx->tm->t_end, &ctx->tm_host->t_end, sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    return WENO_OK;
+}
+
+weno_status weno_step(weno_ctx* ctx, double t_end, double* dt_taken)
+{
+    if (!ctx) return WENO_ERR_INVALID_ARG;
+    weno_status st = read_time(ctx);
+    if (st != WENO_OK) return st;
+    const double t0 = ctx->tm_host->t;
+    if ((st = set_t_end(ctx, t_end)) != WENO_OK) return st;
+    CK(issue_step(ctx, ctx->phase, ctx->stream));
+    st = finish_steps(ctx);
+    if (dt_taken) *dt_taken = ctx->tm_host->t - t0;
+    return st;
+}
+
+weno_status weno_advance(weno_ctx* ctx, double t_end, int max_steps, int* steps_taken)
+{
+    if (!ctx || max_steps < 0) return WENO_ERR_INVALID_ARG;
+    if (steps_taken) *steps_taken = 0;
+    weno_status st = read_time(ctx);
+    if (st != WENO_OK) return st;
+    const long long s0 = ctx->tm_host->steps;
+    if ((st = build_graphs(ctx)) != WENO_OK) return st;
+    if ((st = set_t_end(ctx, t_end)) != WENO_OK) return st;
+    int remaining = max_steps;
+    const int chunk = 64;
+    while (remaining > 0 && ctx->tm_host->status == 0 && ctx->tm_host->t < t_end) {
+        const int k = remaining < chunk ? remaining : chunk;
+        const long long before = ctx->tm_host->steps;
+        for (int i = 0; i < k; ++i) CK(cudaGraphLaunch(ctx->graph[(ctx->phase + i) % 3], ctx->stream));
+        if ((st = read_time(ctx)) != WENO_OK) return st;
+        remaining -= k;
+        if (ctx->tm_host->steps - before < k) break;
+    }
+    if (steps_taken) *steps_taken = (int)(ctx->tm_host->steps - s0);
+    return finish_steps(ctx);
+}
+
+weno_status weno_enqueue_steps(weno_ctx* ctx, double t_end, int nsteps)
+{
+    if (!ctx || nsteps < 0) return WENO_ERR_INVALID_ARG;
+    weno_status st = build_graphs(ctx);
+    if (st != WENO_OK) return st;
+    wis::k_set_tend<<<1, 1, 0, ctx->stream>>>(ctx->tm, t_end);
+    CK(cudaGetLastError());
+    for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(ctx->graph[(ctx->phase + i) % 3], ctx->stream));
+    ctx->phase = (ctx->phase + nsteps) % 3;
+    return WENO_OK;
+}
+
+weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t flush_bytes, double* ms,
+                             unsigned long long* weno_faces)
+{
+    if (!ctx || reps < 1 || !ms) return WENO_ERR_INVALID_ARG;
+    weno_status st = read_time(ctx);
+    if (st != WENO_OK) return st;
+    void* cur = ctx->buf[ctx->phase];
+    for (int d = 0; d < ctx->dim; ++d) {
+        wis::GhostArgs ga = ghost_args(ctx, cur, d);
+        ga.t_fixed = ctx->tm_host->t;
+        CK(do_ghost(ctx, ga, ctx->stream));
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int d = 0; d < ctx->dim; ++d) {
+        double tot = 0.0;
+        unsigned long long wf = 0;
+        for (int r = 0; r < reps; ++r) {
+            if (flush_dev && flush_bytes) CK(cudaMemsetAsync(flush_dev, r & 0xff, flush_bytes, ctx->stream));
+            CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
+            wis::SweepArgs a = sweep_args(ctx, d);
+            a.U = cur;
+            a.mode = wis::MODE_ACC_SET;
+            a.acc = ctx->dim > 1 ? ctx->acc : ctx->rhs_out;
+            if (!a.acc) {
+                st = ensure_rhs_bufs(ctx);
+                if (st != WENO_OK) return st;
+                a.acc = ctx->rhs_out;
+            }
+            CK(cudaEventRecord(e0, ctx->stream));
+            CK(do_sweep(ctx, d, a, ctx->stream));
+            CK(cudaEventRecord(e1, ctx->stream));
+            unsigned long long c = 0;
+            CK(cudaMemcpyAsync(&c, ctx->wcount, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaStreamSynchronize(ctx->stream));
+            float m = 0.f;
+            CK(cudaEventElapsedTime(&m, e0, e1));
+            tot += m;
+            wf = c;
+        }
+        ms[d] = tot / reps;
+        if (weno_faces) weno_faces[d] = wf;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return WENO_OK;
+}
+
+weno_status weno_conserved_totals(weno_ctx* ctx, double* totals)
+{
+    if (!ctx || !totals) return WENO_ERR_INVALID_ARG;
+    weno_status st = read_time(ctx);
+    if (st != WENO_OK) return st;
+    wis::TotArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.U = ctx->buf[ctx->phase];
+    for (int k = 0; k < 3; ++k) a.n[k] = ctx->n[k];
+    a.sy = ctx->sy; a.sz = ctx->sz; a.sv = ctx->sv; a.off0 = ctx->off0;
+    a.partial = ctx->partial;
+    if (ctx->prec == WENO_FP64) CK(wis::totals_f64(ctx->dim, a, ctx->tot_blocks, ctx->stream));
+    else CK(wis::totals_f32(ctx->dim, a, ctx->tot_blocks, ctx->stream));
+    double dV = 1.0;
+    for (int d = 0; d < ctx->dim; ++d) dV *= ctx->dx[d];
+    wis::k_totals_final<<<1, 32, 0, ctx->stream>>>(ctx->partial, ctx->tot_blocks, ctx->nv, dV, ctx->totals_dev);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(totals, ctx->totals_dev, sizeof(double) * ctx->nv, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return WENO_OK;
+}
+
+weno_status weno_weno_face_count(weno_ctx* ctx, unsigned long long* count, int reset)
+{
+    if (!ctx) return WENO_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    CK(cudaMemcpyAsync(&v, ctx->wcount, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (count) *count = v;
+    if (reset) {
+        CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return WENO_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------- FMA peak probe
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T* sink, int iters, T b, T c)
+{
+    T a0 = T(threadIdx.x) * T(1e-3), a1 = a0 + T(1), a2 = a0 + T(2), a3 = a0 + T(3);
+    T a4 = a0 + T(4), a5 = a0 + T(5), a6 = a0 + T(6), a7 = a0 + T(7);
+    for (int i = 0; i < iters; ++i) {
+        a0 = wis::fmaT(a0, b, c); a1 = wis::fmaT(a1, b, c); a2 = wis::fmaT(a2, b, c); a3 = wis::fmaT(a3, b, c);
+        a4 = wis::fmaT(a4, b, c); a5 = wis::fmaT(a5, b, c); a6 = wis::fmaT(a6, b, c); a7 = wis::fmaT(a7, b, c);
+    }
+    const T s = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    if (s == T(-12345)) sink[0] = s;
+}
+
+extern "C" weno_status weno_measure_fma_peak(int precision, double* flops, double* seconds)
+{
+    if (precision != 0 && precision != 1) return WENO_ERR_INVALID_ARG;
+    int dev = 0, nsm = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WENO_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return WENO_ERR_CUDA;
+    void* sink = nullptr;
+    if (cudaMalloc(&sink, 16) != cudaSuccess) return WENO_ERR_CUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = nsm * 8, threads = 256;
+    const int iters = precision == 0 ? 8192 : 262144;
+    float best = 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, 0);
+        if (precision == 0) k_fma_peak<double><<<blocks, threads>>>((double*)sink, iters, 0.999999, 1e-6);
+        else k_fma_peak<float><<<blocks, threads>>>((float*)sink, iters, 0.999999f, 1e-6f);
+        cudaEventRecord(e1, 0);
+        err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    if (err == cudaSuccess) err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (err != cudaSuccess) return WENO_ERR_CUDA;
+    const double fl = 2.0 * 8.0 * (double)iters * blocks * threads;
+    if (flops) *flops = fl / (best * 1e-3);
+    if (seconds) *seconds = best * 1e-3;
+    return WENO_OK;
+}

@@ -1,0 +1,271 @@
+// Device arithmetic of the regularized WENO-IS characteristic flux.
+//
+// Everything here is a __device__ __forceinline__ routine used by the sweep
+// kernels in weno_kernels.cuh.  The order of operations follows the paper
+// (Zhu & Hu, arXiv 1908.02464):
+//   cell_prepare   primitives, physical flux, |eigenvalues| of one cell
+//                  (Eq. goveq4 and its multi-D form)
+//   roe_state      Roe average at x_{j+1/2} (Sec. 2.4 step (1))
+//   proj_all       L^s . x for every field s (Sec. 2.4 step (2)-(3),
+//                  Eq. eqchara), written from the structure of L instead of a
+//                  dense matrix product
+//   back_proj      sum_s R^s w^s (Eq. reconstruction2)
+//   recon          candidate fluxes Eq. eq6, indicators Eq. eq11, L2 error
+//                  terms Eq. eq18 and regularized weights Eq. eq8-r
+//
+// Eigenvector convention (fields ordered u-c, u, shear..., u+c):
+//   R^{u-c} = (1, u - c n, H - u_n c), R^{u} = (1, u, q^2/2),
+//   R^{t}   = (0, e_t, u_t),           R^{u+c} = (1, u + c n, H + u_n c),
+//   L = R^{-1}.  With b1 = (gamma-1)/c^2 and
+//   t1(x) = b1 (q^2/2 x_rho - u . x_m + x_E),  a(x) = (u_n x_rho - x_mn)/c:
+//   L^{u-c} x = (t1 + a)/2,  L^{u} x = x_rho - t1,  L^{t} x = x_mt - u_t x_rho,
+//   L^{u+c} x = (t1 - a)/2.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wis {
+
+// ---------------------------------------------------------------- arithmetic
+// Explicit overloads keep float arithmetic in float (no silent promotion).
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double maxT(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float maxT(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double absT(double a) { return fabs(a); }
+__device__ __forceinline__ float absT(float a) { return fabsf(a); }
+
+template <typename T> struct Ar;
+
+template <> struct Ar<double> {
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+};
+
+template <> struct Ar<float> {
+    static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+};
+
+// ------------------------------------------------------------- cell records
+// Per-cell quantities kept in shared memory for a sweep along direction DIR.
+// Record layout (NQ entries): U[NV], F[NV], u[DIM], H, sqrt(rho),
+// |u_n - c|, |u_n|, |u_n + c|.
+template <int DIM> struct CellLayout {
+    static constexpr int NV = DIM + 2;
+    static constexpr int U = 0;
+    static constexpr int F = NV;
+    static constexpr int VEL = 2 * NV;
+    static constexpr int H = 2 * NV + DIM;
+    static constexpr int SQ = H + 1;
+    static constexpr int LM = H + 2;   // |u_n - c|
+    static constexpr int L0 = H + 3;   // |u_n|
+    static constexpr int LP = H + 4;   // |u_n + c|
+    static constexpr int NQ = H + 5;
+};
+
+// Primitives, physical flux along DIR and |eigenvalues| of one cell.
+// q[k] receives record entry k (see CellLayout).
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void cell_prepare(const T* U, T gamma, T* q)
+{
+    using CL = CellLayout<DIM>;
+    const T gm1 = gamma - T(1);
+    const T rho = U[0];
+    const T irho = Ar<T>::rcp(rho);
+    T vel[DIM];
+    T ke2 = T(0);  // rho |u|^2
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        vel[k] = U[1 + k] * irho;
+        ke2 = fmaT(U[1 + k], vel[k], ke2);
+    }
+    const T E = U[DIM + 1];
+    const T p = gm1 * fmaT(T(-0.5), ke2, E);
+    const T c = Ar<T>::sqrt_(gamma * p * irho);
+    const T un = vel[DIR];
+#pragma unroll
+    for (int v = 0; v < CL::NV; ++v) q[CL::U + v] = U[v];
+    q[CL::F + 0] = U[1 + DIR];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) q[CL::F + 1 + k] = U[1 + k] * un;
+    q[CL::F + 1 + DIR] += p;
+    q[CL::F + DIM + 1] = (E + p) * un;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) q[CL::VEL + k] = vel[k];
+    q[CL::H] = (E + p) * irho;
+    q[CL::SQ] = Ar<T>::sqrt_(rho);
+    q[CL::LM] = absT(un - c);
+    q[CL::L0] = absT(un);
+    q[CL::LP] = absT(un + c);
+}
+
+// ----------------------------------------------------------------- Roe state
+template <typename T, int DIM> struct Roe {
+    T u[DIM];
+    T c, ic;     // sound speed and 1/c
+    T H;
+    T b1, hq2;   // (gamma-1)/c^2, |u|^2/2
+    T rt;        // Roe density sqrt(rho_a rho_b)
+};
+
+// Roe average between the cells whose records start at qa (j) and qb (j+1);
+// get(q, k) reads record entry k.
+template <typename T, int DIM, typename GA, typename GB>
+__device__ __forceinline__ Roe<T, DIM> roe_state(GA get_a, GB get_b, T gamma)
+{
+    using CL = CellLayout<DIM>;
+    Roe<T, DIM> r;
+    const T sa = get_a(CL::SQ), sb = get_b(CL::SQ);
+    const T inv = Ar<T>::rcp(sa + sb);
+    const T wa = sa * inv, wb = sb * inv;
+    T q2 = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        r.u[k] = fmaT(wa, get_a(CL::VEL + k), wb * get_b(CL::VEL + k));
+        q2 = fmaT(r.u[k], r.u[k], q2);
+    }
+    r.H = fmaT(wa, get_a(CL::H), wb * get_b(CL::H));
+    r.hq2 = T(0.5) * q2;
+    const T gm1 = gamma - T(1);
+    const T c2 = gm1 * (r.H - r.hq2);
+    r.ic = Ar<T>::rsqrt_(c2);
+    r.c = c2 * r.ic;
+    r.b1 = gm1 * r.ic * r.ic;
+    r.rt = sa * sb;
+    return r;
+}
+
+// w[s] = L^s . x for all fields.
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void proj_all(const Roe<T, DIM>& r, const T* x, T* w)
+{
+    T dot = r.u[0] * x[1];
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) dot = fmaT(r.u[k], x[1 + k], dot);
+    const T t1 = r.b1 * (fmaT(r.hq2, x[0], x[DIM + 1]) - dot);
+    const T a = fmaT(r.u[DIR], x[0], -x[1 + DIR]) * r.ic;
+    w[0] = T(0.5) * (t1 + a);
+    w[1] = x[0] - t1;
+    int s = 2;
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+        if (t == DIR) continue;
+        w[s] = fmaT(-r.u[t], x[0], x[1 + t]);
+        ++s;
+    }
+    w[DIM + 1] = T(0.5) * (t1 - a);
+}
+
+// out[v] += sum_s R[v][s] w[s]
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void back_proj_add(const Roe<T, DIM>& r, const T* w, T* out)
+{
+    constexpr int LAST = DIM + 1;
+    const T sum = w[0] + w[1] + w[LAST];
+    const T dif = w[LAST] - w[0];
+    out[0] += sum;
+    int s = 2;
+    T eshear = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        T m = r.u[k] * sum;
+        if (k == DIR) {
+            m = fmaT(r.c, dif, m);
+        } else {
+            m += w[s];
+            eshear = fmaT(r.u[k], w[s], eshear);
+            ++s;
+        }
+        out[1 + k] += m;
+    }
+    T e = fmaT(r.H, w[0] + w[LAST], r.u[DIR] * r.c * dif);
+    e = fmaT(r.hq2, w[1], e);
+    out[LAST] += e + eshear;
+}
+
+// --------------------------------------------------- scalar reconstruction
+// f0..f4 = f_{j-2} .. f_{j+2}; lam = c sigma^s (Eq. eq29).  Returns the
+// reconstructed value at x_{j+1/2} with the weights of Eq. eq8-r.
+template <typename T>
+__device__ __forceinline__ T recon(T a, T b, T c, T d, T e, T lam, T eps);
+
+template <>
+__device__ __forceinline__ double recon<double>(double a, double b, double c, double d, double e,
+                                                double lam, double eps)
+{
+    // Eq. eq6
+    const double q0 = 0.5 * (c + d);
+    const double q1 = fmaT(1.5, c, -0.5 * b);
+    const double q2 = fmaT(1.0 / 3.0, c, fmaT(5.0 / 6.0, d, (-1.0 / 6.0) * e));
+    const double q3 = fmaT(1.0 / 3.0, a, fmaT(-7.0 / 6.0, b, (11.0 / 6.0) * c));
+    // Eq. eq11
+    const double b0 = (d - c) * (d - c);
+    const double b1 = (c - b) * (c - b);
+    double t = fmaT(-2.0, d, c) + e;
+    double s = fmaT(-4.0, d, 3.0 * c) + e;
+    const double b2 = fmaT(13.0 / 12.0, t * t, 0.25 * (s * s));
+    t = fmaT(-2.0, b, a) + c;
+    s = fmaT(-4.0, b, a) + 3.0 * c;
+    const double b3 = fmaT(13.0 / 12.0, t * t, 0.25 * (s * s));
+    t = fmaT(-4.0, b + d, a + e) + 6.0 * c;
+    s = fmaT(2.0, b - d, e - a);
+    const double tau = fmaT(13.0 / 12.0, t * t, 0.25 * (s * s));
+    // Eq. eq18 (E_2 = E_3 = 0)
+    t = fmaT(-2.0, c, b + d);
+    const double E = (t * t) * (1.0 / 45.0);
+    // Eq. eq8-r: alpha_k = d_k (D_k + lam tau)/D_k with D_k = lam beta_k + E_k + eps.
+    // The normalized sum sum_k alpha_k q_k / sum_k alpha_k is evaluated
+    // over the common denominator D_0 D_1 D_2 D_3 (one division).
+    const double D0 = fmaT(lam, b0, E + eps);
+    const double D1 = fmaT(lam, b1, E + eps);
+    const double D2 = fmaT(lam, b2, eps);
+    const double D3 = fmaT(lam, b3, eps);
+    const double lt = lam * tau;
+    const double D01 = D0 * D1, D23 = D2 * D3;
+    const double w0 = 0.4 * (D0 + lt) * (D1 * D23);
+    const double w1 = 0.2 * (D1 + lt) * (D0 * D23);
+    const double w2 = 0.3 * (D2 + lt) * (D01 * D3);
+    const double w3 = 0.1 * (D3 + lt) * (D01 * D2);
+    const double num = fmaT(w0, q0, fmaT(w1, q1, fmaT(w2, q2, w3 * q3)));
+    const double den = (w0 + w1) + (w2 + w3);
+    return num / den;
+}
+
+template <>
+__device__ __forceinline__ float recon<float>(float a, float b, float c, float d, float e,
+                                              float lam, float eps)
+{
+    const float q0 = 0.5f * (c + d);
+    const float q1 = fmaT(1.5f, c, -0.5f * b);
+    const float q2 = fmaT(1.0f / 3.0f, c, fmaT(5.0f / 6.0f, d, (-1.0f / 6.0f) * e));
+    const float q3 = fmaT(1.0f / 3.0f, a, fmaT(-7.0f / 6.0f, b, (11.0f / 6.0f) * c));
+    const float b0 = (d - c) * (d - c);
+    const float b1 = (c - b) * (c - b);
+    float t = fmaT(-2.0f, d, c) + e;
+    float s = fmaT(-4.0f, d, 3.0f * c) + e;
+    const float b2 = fmaT(13.0f / 12.0f, t * t, 0.25f * (s * s));
+    t = fmaT(-2.0f, b, a) + c;
+    s = fmaT(-4.0f, b, a) + 3.0f * c;
+    const float b3 = fmaT(13.0f / 12.0f, t * t, 0.25f * (s * s));
+    t = fmaT(-4.0f, b + d, a + e) + 6.0f * c;
+    s = fmaT(2.0f, b - d, e - a);
+    const float tau = fmaT(13.0f / 12.0f, t * t, 0.25f * (s * s));
+    t = fmaT(-2.0f, c, b + d);
+    const float E = (t * t) * (1.0f / 45.0f);
+    // In float the product of four denominators can underflow (eps = 1e-20),
+    // so each ratio lam tau / D_k takes its own reciprocal.
+    const float lt = lam * tau;
+    const float a0 = 0.4f * fmaT(lt, __fdividef(1.0f, fmaT(lam, b0, E + eps)), 1.0f);
+    const float a1 = 0.2f * fmaT(lt, __fdividef(1.0f, fmaT(lam, b1, E + eps)), 1.0f);
+    const float a2 = 0.3f * fmaT(lt, __fdividef(1.0f, fmaT(lam, b2, eps)), 1.0f);
+    const float a3 = 0.1f * fmaT(lt, __fdividef(1.0f, fmaT(lam, b3, eps)), 1.0f);
+    const float num = fmaT(a0, q0, fmaT(a1, q1, fmaT(a2, q2, a3 * q3)));
+    const float den = (a0 + a1) + (a2 + a3);
+    return num / den;
+}
+
+}  // namespace wis

@@ -1,0 +1,23 @@
+// FP32 instantiations: float storage and arithmetic (the CFL max, the time
+// step, the time and the conserved totals stay in double).
+#include "weno_launch.cuh"
+
+namespace wis {
+
+cudaError_t sweep_f32(int dim, int dir, const SweepArgs& a, cudaStream_t s)
+{
+    return launch_sweep_t<float, false>(dim, dir, a, s);
+}
+cudaError_t ghost_f32(int dim, const GhostArgs& a, cudaStream_t s) { return launch_ghost_t<float>(dim, a, s); }
+cudaError_t cfl_f32(int dim, const CflArgs& a, int nsm, cudaStream_t s) { return launch_cfl_t<float>(dim, a, nsm, s); }
+cudaError_t totals_f32(int dim, const TotArgs& a, int blocks, cudaStream_t s)
+{
+    return launch_totals_t<float>(dim, a, blocks, s);
+}
+cudaError_t pack_f32(const void* src, void* dst, int nv, const int* n, long long sy, long long sz, long long sv,
+                     long long off0, int to_ghosted, int nsm, cudaStream_t s)
+{
+    return launch_pack_t<float>(src, dst, nv, n, sy, sz, sv, off0, to_ghosted, nsm, s);
+}
+
+}  // namespace wis

@@ -1,0 +1,127 @@
+// Launch helpers: tile shapes per (dim, direction) and the host-side wrappers
+// that pick a kernel instantiation.  Included by one translation unit per
+// arithmetic (weno_f64.cu, weno_f32.cu, weno_mixed.cu) so that the three
+// precisions compile in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "weno_kernels.cuh"
+
+namespace wis {
+
+// Tile shapes.  x-sweeps take LINES rows of SEG contiguous cells; y/z sweeps
+// take 32 consecutive x-columns (one coalesced 32-element row per cell
+// position) of SEG cells along the sweep.
+template <int DIM, int DIR> struct Tile;
+template <> struct Tile<1, 0> { static constexpr int LINES = 1, SEG = 128, NT = 128; };
+template <> struct Tile<2, 0> { static constexpr int LINES = 4, SEG = 64, NT = 256; };
+template <> struct Tile<2, 1> { static constexpr int LINES = 32, SEG = 8, NT = 256; };
+template <> struct Tile<3, 0> { static constexpr int LINES = 4, SEG = 64, NT = 256; };
+template <> struct Tile<3, 1> { static constexpr int LINES = 32, SEG = 8, NT = 256; };
+template <> struct Tile<3, 2> { static constexpr int LINES = 32, SEG = 8, NT = 256; };
+
+template <typename T, int DIM, int DIR, bool DET64>
+cudaError_t launch_sweep_one(const SweepArgs& a, cudaStream_t s)
+{
+    using TL = Tile<DIM, DIR>;
+    using SM = SweepSmem<T, DIM, TL::LINES, TL::SEG>;
+    auto kern = k_sweep<T, DIM, DIR, TL::LINES, TL::SEG, TL::NT, DET64>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int nd = a.n[DIR];
+    const int segs = (nd + TL::SEG - 1) / TL::SEG;
+    dim3 grid;
+    if (DIR == 0) grid = dim3(segs, (a.n[1] + TL::LINES - 1) / TL::LINES, a.n[2]);
+    else if (DIR == 1) grid = dim3((a.n[0] + TL::LINES - 1) / TL::LINES, segs, a.n[2]);
+    else grid = dim3((a.n[0] + TL::LINES - 1) / TL::LINES, a.n[1], segs);
+    kern<<<grid, TL::NT, SM::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, bool DET64>
+cudaError_t launch_sweep_t(int dim, int dir, const SweepArgs& a, cudaStream_t s)
+{
+    if (dim == 1) return launch_sweep_one<T, 1, 0, DET64>(a, s);
+    if (dim == 2) {
+        if (dir == 0) return launch_sweep_one<T, 2, 0, DET64>(a, s);
+        return launch_sweep_one<T, 2, 1, DET64>(a, s);
+    }
+    if (dir == 0) return launch_sweep_one<T, 3, 0, DET64>(a, s);
+    if (dir == 1) return launch_sweep_one<T, 3, 1, DET64>(a, s);
+    return launch_sweep_one<T, 3, 2, DET64>(a, s);
+}
+
+inline int grid_for(long long work, int threads, int cap)
+{
+    long long b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+template <typename T>
+cudaError_t launch_ghost_t(int dim, const GhostArgs& a, cudaStream_t s)
+{
+    long long P;
+    if (a.dir == 0) P = (long long)a.n[1] * a.n[2];
+    else if (a.dir == 1) P = (long long)a.n[0] * a.n[2];
+    else P = (long long)a.n[0] * a.n[1];
+    const int blocks = grid_for(6 * P, 256, 4096);
+    if (dim == 1) k_ghost<T, 1><<<blocks, 256, 0, s>>>(a);
+    else if (dim == 2) k_ghost<T, 2><<<blocks, 256, 0, s>>>(a);
+    else k_ghost<T, 3><<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cfl_t(int dim, const CflArgs& a, int nsm, cudaStream_t s)
+{
+    const long long cells = (long long)a.n[0] * a.n[1] * a.n[2];
+    const int blocks = grid_for(cells, 256, nsm * 8);
+    if (dim == 1) k_cfl<T, 1><<<blocks, 256, 0, s>>>(a);
+    else if (dim == 2) k_cfl<T, 2><<<blocks, 256, 0, s>>>(a);
+    else k_cfl<T, 3><<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_totals_t(int dim, const TotArgs& a, int blocks, cudaStream_t s)
+{
+    if (dim == 1) k_totals<T, 1><<<blocks, 256, 0, s>>>(a);
+    else if (dim == 2) k_totals<T, 2><<<blocks, 256, 0, s>>>(a);
+    else k_totals<T, 3><<<blocks, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pack_t(const void* src, void* dst, int nv, const int* n, long long sy, long long sz,
+                          long long sv, long long off0, int to_ghosted, int nsm, cudaStream_t s)
+{
+    const long long total = (long long)nv * n[0] * n[1] * n[2];
+    const int blocks = grid_for(total, 256, nsm * 16);
+    k_pack<T><<<blocks, 256, 0, s>>>(reinterpret_cast<const T*>(src), reinterpret_cast<T*>(dst), nv, n[0],
+                                      n[1], n[2], sy, sz, sv, off0, to_ghosted);
+    return cudaGetLastError();
+}
+
+// per-precision entry points (one translation unit each)
+cudaError_t sweep_f64(int dim, int dir, const SweepArgs& a, cudaStream_t s);
+cudaError_t sweep_f32(int dim, int dir, const SweepArgs& a, cudaStream_t s);
+cudaError_t sweep_mixed(int dim, int dir, const SweepArgs& a, cudaStream_t s);
+cudaError_t ghost_f64(int dim, const GhostArgs& a, cudaStream_t s);
+cudaError_t ghost_f32(int dim, const GhostArgs& a, cudaStream_t s);
+cudaError_t cfl_f64(int dim, const CflArgs& a, int nsm, cudaStream_t s);
+cudaError_t cfl_f32(int dim, const CflArgs& a, int nsm, cudaStream_t s);
+cudaError_t totals_f64(int dim, const TotArgs& a, int blocks, cudaStream_t s);
+cudaError_t totals_f32(int dim, const TotArgs& a, int blocks, cudaStream_t s);
+cudaError_t pack_f64(const void* src, void* dst, int nv, const int* n, long long sy, long long sz, long long sv,
+                     long long off0, int to_ghosted, int nsm, cudaStream_t s);
+cudaError_t pack_f32(const void* src, void* dst, int nv, const int* n, long long sy, long long sz, long long sv,
+                     long long off0, int to_ghosted, int nsm, cudaStream_t s);
+
+}  // namespace wis

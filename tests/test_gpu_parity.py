@@ -1,0 +1,277 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bar: FP64 right-hand sides agree with the oracle to 1e-12 normwise-relative
+per conserved variable (max |gpu - oracle| <= 1e-12 max |oracle|); full runs
+to 1e-10 in L1 of density at the final time; hybrid flags agree face by face
+except where the oracle's sigma sits within 1e-9 (relative) of the threshold
+eps_h, where both decisions are correct to rounding.
+
+Conditioning: on WENO faces a field whose own data are smooth has a detector
+value dv^s made of rounding noise (a fifth difference, then a projection that
+cancels), and with lambda beta_k comparable to eps = 1e-20 the weights of
+Eq. eq8-r depend on that noise at first order.  There the oracle itself moves
+by up to a few 1e-12 when its input is perturbed by one ulp.  Where the strict
+1e-12 bar fails, the test measures that sensitivity (three random one-ulp
+perturbations of the input) and requires the GPU to stay within ten times it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1908_02464_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1908_02464_gb300 import weno  # noqa: E402
+
+RTOL64 = 1e-12
+
+
+def _gpu_rhs(prob, U, precision="fp64", t=0.0):
+    s = weno.Solver(prob, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    Ud = torch.from_numpy(U).to("cuda", dt)
+    r = s.rhs(Ud, t)
+    flags = s.face_flags(Ud, t)
+    torch.cuda.synchronize()
+    out = r.double().cpu().numpy(), flags.cpu().numpy()
+    s.close()
+    return out
+
+
+def _compare_rhs(prob, U, t=0.0, rtol=RTOL64, precision="fp64"):
+    ref, oflags, ratio = orc.rhs(prob, U, t, want_flags=True)
+    got, gflags = _gpu_rhs(prob, U, precision, t)
+    mism = np.nonzero(gflags != oflags)[0]
+    near = np.abs(ratio[mism] - 1.0) < 1e-9
+    assert np.all(near), f"{len(mism)} flag mismatches, ratios {ratio[mism][:5]}"
+    nv = U.shape[0]
+    scale = np.max(np.abs(ref).reshape(nv, -1), axis=1)
+    rel = np.max(np.abs(got - ref).reshape(nv, -1), axis=1) / scale
+    if len(mism) == 0 and np.all(rel <= rtol):
+        return rel, float(np.mean(oflags)), 0
+    # the oracle's own sensitivity to one-ulp input perturbations
+    rng = np.random.default_rng(12345)
+    kappa = np.zeros(nv)
+    for _ in range(3):
+        Up = U * (1.0 + 2.220446049250313e-16 * rng.choice([-1.0, 0.0, 1.0], size=U.shape))
+        rp = orc.rhs(prob, Up, t)
+        kappa = np.maximum(kappa, np.max(np.abs(rp - ref).reshape(nv, -1), axis=1) / scale)
+    tol = np.maximum(rtol, 10.0 * kappa)
+    assert np.all(rel <= tol), (rel, kappa)
+    return rel, float(np.mean(oflags)), len(mism)
+
+
+# ------------------------------------------------------------------ RHS
+
+@pytest.mark.parametrize("kind", ["smooth", "mixed", "jumps"])
+@pytest.mark.parametrize("n", [[300], [7], [129]])
+def test_rhs_parity_1d(kind, n):
+    prob, U = P.random_state(1, n, seed=100 + n[0], kind=kind)
+    _compare_rhs(prob, U)
+
+
+@pytest.mark.parametrize("kind", ["smooth", "mixed", "jumps"])
+@pytest.mark.parametrize("n", [[150, 37], [64, 8], [33, 70]])
+def test_rhs_parity_2d(kind, n):
+    prob, U = P.random_state(2, n, seed=200 + n[0], kind=kind)
+    _compare_rhs(prob, U)
+
+
+@pytest.mark.parametrize("kind", ["smooth", "mixed", "jumps"])
+def test_rhs_parity_3d(kind):
+    prob, U = P.random_state(3, [70, 20, 13], seed=300, kind=kind)
+    _compare_rhs(prob, U)
+
+
+def test_rhs_parity_hybrid_off():
+    prob, U = P.random_state(2, [40, 24], seed=5, kind="mixed")
+    prob["hybrid"] = 0
+    rel, frac, _ = _compare_rhs(prob, U)
+    assert frac == 0.0
+
+
+def test_rhs_parity_boundaries():
+    """Shock tubes (transmissive), blast waves with reflecting walls (LLF on
+    the GPU path), double Mach reflection (inflow, DMR bottom/top at t>0)."""
+    prob, U = P.sod(200)
+    _compare_rhs(prob, U)
+    prob, U = P.shu_osher(400)
+    _compare_rhs(prob, U)
+    prob, U = P.blast_waves(256)
+    prob["splitting"] = "llf"
+    _compare_rhs(prob, U)
+    prob, U = P.double_mach(96, 24)
+    _compare_rhs(prob, U, t=0.013)
+
+
+def test_rhs_parity_double_mach_full_size():
+    """The 2048 x 512 double Mach reflection at the size the benchmark times."""
+    prob, U = P.double_mach(2048, 512)
+    _compare_rhs(prob, U, t=0.0)
+
+
+def _oracle_rhs_at(prob, U, cells, rng=None):
+    """Oracle RHS at sampled cells of a periodic grid, face by face.  With
+    rng, every gathered stencil value is perturbed by one ulp at random."""
+    dim = prob["dim"]
+    nv = dim + 2
+    n = prob["n"]
+    out = []
+    for c in cells:   # c = (i, j, k)
+        r = np.zeros(nv)
+        for d in range(dim):
+            dx = (prob["hi"][d] - prob["lo"][d]) / n[d]
+            eh = orc.eps_h(prob, d)
+            F = []
+            for face in (c[d], c[d] + 1):   # faces i-1/2 and i+1/2
+                six = []
+                for m in range(face - 3, face + 3):
+                    idx = list(c)
+                    idx[d] = m % n[d]
+                    six.append(U[(slice(None),) + tuple(reversed(idx))])
+                six = np.stack(six)
+                if rng is not None:
+                    six = six * (1.0 + 2.220446049250313e-16 * rng.choice([-1.0, 0.0, 1.0], size=six.shape))
+                Fh, _, _ = orc.face_flux(prob, d, six, eps_h=eh)
+                F.append(Fh)
+            r -= (F[1] - F[0]) / dx
+        out.append(r)
+    return np.array(out)
+
+
+def test_rhs_parity_vortex_3d_full_size_sampled():
+    """256^3 periodic vortex: GPU RHS against the oracle at sampled cells."""
+    prob, U = P.vortex3d(256)
+    got, _ = _gpu_rhs(prob, U)
+    rng = np.random.default_rng(0)
+    cells = [tuple(int(x) for x in rng.integers(0, 256, size=3)) for _ in range(64)]
+    ref = _oracle_rhs_at(prob, U, cells)
+    g = np.array([got[(slice(None),) + tuple(reversed(c))] for c in cells])
+    scale = np.max(np.abs(got).reshape(5, -1), axis=1)
+    err = np.max(np.abs(g - ref), axis=0)
+    # p = 100 makes the momentum and energy fluxes ~100 while their divergence
+    # is O(0.1): the oracle's own one-ulp sensitivity sets the bar there
+    prng = np.random.default_rng(7)
+    kappa = np.zeros(5)
+    for _ in range(3):
+        kappa = np.maximum(kappa, np.max(np.abs(_oracle_rhs_at(prob, U, cells, prng) - ref), axis=0))
+    assert np.all(err <= np.maximum(RTOL64 * scale, 10.0 * kappa)), (err, kappa, scale)
+
+
+# ------------------------------------------------------------------ steps
+
+def _run_gpu(prob, U, precision="fp64", use_advance=True):
+    s = weno.Solver(prob, precision)
+    s.set_state(U)
+    if use_advance:
+        k = s.advance(prob["t_end"])
+    else:
+        k = 0
+        while s.time()[0] < prob["t_end"]:
+            s.step(prob["t_end"])
+            k += 1
+    V, t = s.get_state()
+    s.close()
+    return V.astype(np.float64), t, k
+
+
+@pytest.mark.parametrize("fn", [P.sod, P.shu_osher, P.lax])
+def test_full_run_parity_1d(fn):
+    prob, U = fn()
+    Uo = U.copy()
+    st, to, ko = orc.advance(prob, Uo, 0.0, prob["t_end"])
+    assert st == 0
+    V, t, k = _run_gpu(prob, U)
+    assert t == to and k == ko
+    n = prob["n"][0]
+    l1 = np.sum(np.abs(V[0] - Uo[0])) / n
+    assert l1 <= 1e-10, l1
+
+
+def test_double_mach_steps_parity():
+    prob, U = P.double_mach(128, 32)
+    prob["t_end"] = 0.01
+    Uo = U.copy()
+    st, to, ko = orc.advance(prob, Uo, 0.0, prob["t_end"])
+    V, t, k = _run_gpu(prob, U)
+    assert k == ko and t == to
+    assert np.mean(np.abs(V[0] - Uo[0])) <= 1e-10
+    assert np.max(np.abs(V - Uo)) <= 1e-9 * np.max(np.abs(Uo))
+
+
+def test_step_equals_advance_bitwise():
+    prob, U = P.shu_osher(400)
+    prob["t_end"] = 0.3
+    A, ta, ka = _run_gpu(prob, U, use_advance=True)
+    B, tb, kb = _run_gpu(prob, U, use_advance=False)
+    assert ka == kb and ta == tb
+    assert np.array_equal(A, B)
+
+
+def test_totals_match_oracle_and_are_conserved():
+    prob, U = P.random_state(2, [48, 40], seed=9, kind="mixed")
+    s = weno.Solver(prob)
+    s.set_state(U)
+    t0 = s.totals()
+    assert np.allclose(t0, orc.totals(prob, U), rtol=1e-13, atol=1e-15)
+    s.advance(1.0, max_steps=6)
+    assert s.time()[1] == 6
+    assert np.allclose(s.totals(), t0, rtol=1e-13, atol=1e-14)
+    s.close()
+
+
+def test_nonphysical_state_reports_and_keeps_last_good_state():
+    prob, U = P.sod(64)
+    U = U.copy()
+    U[2, 20] = -1.0
+    s = weno.Solver(prob)
+    s.set_state(U)
+    with pytest.raises(weno.WenoError) as e:
+        s.step(0.2)
+    assert e.value.status == weno.WENO_ERR_NONPHYSICAL
+    V, t = s.get_state()
+    assert t == 0.0 and np.array_equal(V, U)
+    s.close()
+
+
+def test_weno_face_counter_matches_flags():
+    prob, U = P.shu_osher(400)
+    s = weno.Solver(prob)
+    Ud = torch.from_numpy(U).cuda()
+    s.weno_faces(reset=True)
+    flags = s.face_flags(Ud)
+    torch.cuda.synchronize()
+    assert s.weno_faces() == int((flags == 0).sum())
+    s.close()
+
+
+# ------------------------------------------------------------------ FP32 / mixed
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_reduced_precision_rhs_close(precision):
+    prob, U = P.random_state(2, [64, 48], seed=21, kind="mixed")
+    ref = orc.rhs(prob, U)
+    got, _ = _gpu_rhs(prob, U, precision)
+    rel = np.max(np.abs(got - ref).reshape(4, -1), axis=1) / np.max(np.abs(ref).reshape(4, -1), axis=1)
+    assert np.all(rel < 1e-3), rel
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_reduced_precision_sod_accuracy(precision):
+    prob, U = P.sod(200)
+    V, t, k = _run_gpu(prob, U, precision)
+    W = orc.riemann_sample(1.4, prob["WL"], prob["WR"], 0.5, 0.2, P.centers(0, 1, 200))
+    assert np.mean(np.abs(V[0] - W[0])) < 5e-3
+
+
+def test_measure_fma_peak_runs():
+    f64, s64 = weno.weno_measure_fma_peak(0)
+    f32, s32 = weno.weno_measure_fma_peak(1)
+    assert f64 > 1e11 and f32 > 1e13 and s64 > 0 and s32 > 0
