@@ -1,0 +1,348 @@
+"""Benchmark: Euler RHS cell-updates/s of the regularized WENO-IS solver on GB300.
+
+Workload: the double Mach reflection of Sec. 4.5 of the paper on a 2048 x 512
+grid (LLF splitting, hybrid on, RK3 at CFL 0.5), synthetic initial data as the
+paper defines them, advanced on the GPU from t = 0 to t = 0.05 (untimed) so
+that the Mach stem, slip line and reflected shocks are present.  A step is one
+full RK3 step (CFL max-reduction, three stages of ghost cells + x/y sweeps
+with the RK combination fused); one step is 3 cell-updates per cell.
+
+`value` is the FP64 path.  The FP32 and mixed paths are timed on the same
+state and reported with their L1/Linf density error against the FP64 path
+after the same number of steps.  L2 is flushed (256 MiB write) between timed
+steps.  `--impl reference` times the FP64 CPU oracle (the reference arm of
+this project) on the same grid from the initial condition.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Euler RHS cell-updates/s on 1 GB300 (FP64 vs FP32), % roofline, L1 err vs FP64"
+UNIT = "cell-updates/s"
+NX, NY = 2048, 512
+T_DEVELOP = 0.05
+
+# Algorithmic flops (add/sub, mul, div, sqrt each count one) of the method as
+# written in the paper, from the operation-counting instantiation of the CPU
+# oracle: per cell (primitives + physical flux of one sweep direction), per
+# linear-upwind face and per WENO face, by dimension.  The flux divergence
+# adds 2 flops per variable per cell.
+ALG_FLOPS = {1: (18, 158, 1139), 2: (22, 221, 1625), 3: (26, 292, 2167)}
+FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA lanes per SM per clock on GB300
+FP32_FLOP_PER_CLK_SM = 256    # 128 FFMA lanes per SM per clock
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1908_02464_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = str(index)
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(index).uuid)
+            self.index = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", self.index], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def sweep_flops(dim: int, n, weno_faces: int, d: int) -> float:
+    fc, fu, fw = ALG_FLOPS[dim]
+    cells = float(np.prod(n))
+    faces = cells / n[d] * (n[d] + 1)
+    return cells * (fc + 2 * (dim + 2)) + faces * fu + weno_faces * (fw - fu)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args) -> dict:
+    import torch
+    from paper_1908_02464_gb300 import problems as P
+    from paper_1908_02464_gb300 import weno
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.cuda.current_device()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    cells = NX * NY
+    prob, U0 = P.double_mach(NX, NY)
+    stream = torch.cuda.current_stream()
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    # developed state (untimed)
+    s64 = weno.Solver(prob, "fp64", stream=stream)
+    s64.set_state(U0)
+    s64.advance(T_DEVELOP)
+    Udev, t_dev = s64.get_state(device=True)
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")   # 256 MiB
+
+    def timed(solver, K, W):
+        solver.set_state(Udev, t_dev)
+        solver.enqueue_steps(1.0, W)
+        torch.cuda.synchronize()
+        solver.weno_faces(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(f"timed_{solver.precision}")
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            solver.enqueue_steps(1.0, 1)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        wf = solver.weno_faces()
+        return ms, wf
+
+    ms64, wf64 = timed(s64, args.steps, args.warmup)
+    tot = sum(ms64)
+    if ws > 1:
+        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot = float(t.item())
+    value = ws * 3.0 * cells * args.steps / (tot * 1e-3)
+    U64, t64 = s64.get_state()
+    n_faces_step = 3 * ((NX + 1) * NY + NX * (NY + 1))
+    weno_frac = wf64 / (n_faces_step * args.steps)
+
+    # dominant kernel: per-direction sweep times on the state after the timed steps
+    torch.cuda.nvtx.range_push("sweeps_fp64")
+    ms_dir, wf_dir = s64.time_sweeps(reps=args.sweep_reps, flush=flush)
+    torch.cuda.nvtx.range_pop()
+    dom = int(np.argmax(ms_dir))
+    fl = sweep_flops(2, [NX, NY], wf_dir[dom], dom)
+    achieved = fl / (ms_dir[dom] * 1e-3)
+    peak64 = nsm * FP64_FLOP_PER_CLK_SM * sm_max * 1e6
+    micro64, _ = weno.weno_measure_fma_peak(0)
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            tj = json.load(f)
+        if tj.get("csrc_digest") == csrc_digest():
+            traffic = tj.get("fp64", {}).get(f"sweep_dir{dom}")
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak64, "traffic": traffic,
+                "kernel": f"k_sweep<double,2,{dom}> ({'x' if dom == 0 else 'y'}-sweep)",
+                "kernel_ms": ms_dir[dom], "alg_flops_per_launch": fl, "weno_faces_per_launch": int(wf_dir[dom]),
+                "peak_source": f"derived: {nsm} SMs x {FP64_FLOP_PER_CLK_SM} FP64 flop/clk x {sm_max:.0f} MHz",
+                "peak_fma_microbenchmark": micro64 / 1e12, "sweep_ms_per_dir": ms_dir,
+                "sweep_share_of_step": 3 * sum(ms_dir) / (tot / args.steps)}
+
+    # reduced-precision paths on the same state
+    extra = {}
+    if not args.fp64_only:
+        for prec in ("fp32", "mixed"):
+            sp = weno.Solver(prob, prec, stream=stream)
+            msp, wfp = timed(sp, args.steps, args.warmup)
+            Up, tp_ = sp.get_state()
+            totp = sum(msp)
+            d = np.abs(Up[0].astype(np.float64) - U64[0])
+            ms_d, wf_d = sp.time_sweeps(reps=5, flush=flush)
+            dd = int(np.argmax(ms_d))
+            flp = sweep_flops(2, [NX, NY], wf_d[dd], dd)
+            peak32 = nsm * FP32_FLOP_PER_CLK_SM * sm_max * 1e6
+            extra[prec] = {"value": ws * 3.0 * cells * args.steps / (totp * 1e-3), "ms_per_step": totp / args.steps,
+                           "l1_rho_vs_fp64": float(np.mean(d)), "linf_rho_vs_fp64": float(np.max(d)),
+                           "weno_face_fraction": wfp / (n_faces_step * args.steps),
+                           "t_after": tp_, "t_fp64_after": t64,
+                           "roofline": {"bound": "alu", "achieved": flp / (ms_d[dd] * 1e-3) / 1e12,
+                                        "peak": peak32 / 1e12, "unit": "TFLOP/s",
+                                        "frac": flp / (ms_d[dd] * 1e-3) / peak32,
+                                        "kernel_ms": ms_d[dd], "sweep_ms_per_dir": ms_d}}
+            sp.close()
+
+    clk = clocks.stop()
+    clk["window"] = "development run + all timed regions (FP64, FP32, mixed)"
+
+    # end to end through the public API with pinned host buffers
+    e2e_steps = min(args.steps, 10)
+    Uh = torch.from_numpy(np.ascontiguousarray(U64)).pin_memory()
+    Uo = torch.empty_like(Uh).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tcur = t64
+    for _ in range(e2e_steps):
+        s64.set_state(Uh, tcur)
+        s64.step(1.0)
+        tcur = weno.weno_get_state(s64.ctx, Uo)
+        Uh, Uo = Uo, Uh
+    el = time.perf_counter() - t0
+    e2e = {"value": ws * 3.0 * cells * e2e_steps / el, "unit": UNIT, "h2d_bytes_per_step": Uh.numel() * 8,
+           "d2h_bytes_per_step": Uh.numel() * 8, "steps": e2e_steps,
+           "api": "weno_set_state(host) + weno_step + weno_get_state(host)"}
+    s64.close()
+
+    launches_per_step = 3 + 3 * 2 * 2 + 1   # cfl, dt, post, 3 x (2 ghosts + 2 sweeps), set_tend
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"double Mach reflection {NX}x{NY} (Sec. 4.5), FP64, state developed on the GPU "
+                                  f"from t=0 to t={T_DEVELOP}, LLF splitting, hybrid on, TVD RK3 CFL 0.5",
+                      "grid": [NX, NY], "cells": cells, "precision": "fp64", "parallelism": f"replicas x{ws}",
+                      "l2": "flushed between timed steps (256 MiB write)",
+                      "weno_face_fraction": weno_frac, "t_start": t_dev, "t_after": t64},
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+           "clocks": clk, "ms_per_step_all": ms64}
+    res.update(extra)
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return res if rank == 0 else None
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_steps(nsteps: int, U=None, t=0.0):
+    from oracle import oracle as orc
+    from paper_1908_02464_gb300 import problems as P
+    prob, U0 = P.double_mach(NX, NY)
+    U = U0 if U is None else U
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        st, t, dt = orc.step(prob, U, t, 1.0)
+    return time.perf_counter() - t0, U, t
+
+
+def cpu_baseline(args) -> dict:
+    steps = args.cpu_steps
+    el, _, _ = oracle_steps(steps)
+    return {"value": 3.0 * NX * NY * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64 RK3 steps of the {NX}x{NY} double Mach reflection from its initial "
+                      f"condition, single-threaded C++ oracle ({el:.1f} s)"}
+
+
+def run_reference(args) -> dict | None:
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return None
+    from oracle import oracle as orc
+    orc.build()
+    from paper_1908_02464_gb300 import problems as P
+    prob, U = P.double_mach(NX, NY)
+    t = 0.0
+    for _ in range(args.warmup):
+        st, t, dt = orc.step(prob, U, t, 1.0)
+    el, U, t = oracle_steps(args.steps, U, t)
+    v = 3.0 * NX * NY * args.steps / el
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"double Mach reflection {NX}x{NY} (Sec. 4.5), FP64, from the initial "
+                                   "condition, LLF splitting, hybrid on, TVD RK3 CFL 0.5",
+                       "grid": [NX, NY], "cells": NX * NY, "precision": "fp64"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.warmup}+{args.steps} RK3 steps of the full grid from t=0"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--fp64-only", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep-reps", type=int, default=5)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        from paper_1908_02464_gb300 import build as B
+        B.build()
+        from oracle import oracle as orc
+        orc.build()
+        res = run_ours(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()
