@@ -168,6 +168,32 @@ weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t fl
  * accumulated in double.  Synchronizes. */
 weno_status weno_conserved_totals(weno_ctx* ctx, double* totals);
 
+/* Allocation-free conserved totals (the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory where they need
+ * the totals: code running while a stream is being captured into a CUDA
+ * graph, applications whose device memory belongs to their own pool, loops
+ * with a fixed memory budget).  Same sums as weno_conserved_totals, for a
+ * state the caller owns and without a context; nothing is allocated.
+ *   dim, n[dim], dx[dim]: grid (cells per direction, spacing); the result is
+ *       sum_cells U dV with dV = prod dx.
+ *   precision: element type of U_dev (double for WENO_FP64, float else).
+ *   U_dev: device array, interior cells only, [nvar][nz][ny][nx], nvar = dim+2.
+ *   totals_dev: device array of nvar doubles, overwritten.
+ *   stream: cudaStream_t cast to void* (NULL = legacy default stream).
+ * The per-block partial sums live in one file-scope device array of 640 KiB
+ * (16384 blocks x 5 variables, 4096 cells per block) that every GPU loading
+ * the library keeps until the process exits; grids of more than 67,108,864
+ * cells are rejected with WENO_ERR_INVALID_ARG, as are a bad dim, n < 1, an
+ * unknown precision or a NULL pointer.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Each call
+ * overwrites the partial sums it uses before reading them, but all calls on a
+ * device share the one array: calls that overlap on the GPU (different
+ * streams without ordering) race.  Asynchronous; WENO_ERR_CUDA if the
+ * address lookup or a launch fails. */
+weno_status weno_conserved_totals_noalloc(int dim, const int* n, const double* dx, int precision,
+                                          const void* U_dev, double* totals_dev, void* stream);
+
 /* Number of faces computed with the WENO (non-linear) flux since the last
  * call with reset != 0, over every sweep launched by weno_rhs, weno_step
  * and weno_advance.  Synchronizes. */

@@ -64,6 +64,7 @@ SIGNATURES = {
     "weno_last_error": (ctypes.c_char_p, [_vp]),
     "weno_measure_fma_peak": (ctypes.c_int, [_ip, _dp, _dp]),
     "weno_enqueue_steps": (ctypes.c_int, [_vp, ctypes.c_double, _ip]),
+    "weno_conserved_totals_noalloc": (ctypes.c_int, [_ip, ctypes.POINTER(_ip), _dp, _ip, _vp, _vp, _vp]),
     "weno_time_sweeps": (ctypes.c_int, [_vp, _ip, _vp, ctypes.c_size_t, _dp, ctypes.POINTER(ctypes.c_ulonglong)]),
 }
 
@@ -183,6 +184,15 @@ def weno_measure_fma_peak(precision: int = 0):
     s = ctypes.c_double(0.0)
     _check(load().weno_measure_fma_peak(int(precision), ctypes.byref(f), ctypes.byref(s)))
     return f.value, s.value
+
+
+def weno_conserved_totals_noalloc(dim: int, n, dx, precision: str, U_dev, totals_dev, stream: int = 0) -> None:
+    """Totals of a caller-owned device state into a caller-owned device buffer,
+    with no allocation (see include/weno_is.h)."""
+    nn = (ctypes.c_int * 3)(*(list(n) + [1] * (3 - len(n))))
+    dd = (ctypes.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx))))
+    _check(load().weno_conserved_totals_noalloc(int(dim), nn, dd, PRECISIONS[precision], _vp(_ptr(U_dev)),
+                                                _vp(_ptr(totals_dev)), _vp(stream or None)))
 
 
 def weno_enqueue_steps(ctx: int, t_end: float, nsteps: int) -> None:
