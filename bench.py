@@ -156,8 +156,11 @@ def run_ours(args) -> dict:
     Udev, t_dev = s64.get_state(device=True)
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")   # 256 MiB
 
+    tiles = {}
+
     def timed(solver, K, W):
         solver.set_state(Udev, t_dev)
+        tiles[solver.precision] = solver.autotune(3)
         solver.enqueue_steps(1.0, W)
         torch.cuda.synchronize()
         solver.weno_faces(reset=True)
@@ -264,7 +267,8 @@ def run_ours(args) -> dict:
                                   f"from t=0 to t={T_DEVELOP}, LLF splitting, hybrid on, TVD RK3 CFL 0.5",
                       "grid": [NX, NY], "cells": cells, "precision": "fp64", "parallelism": f"replicas x{ws}",
                       "l2": "flushed between timed steps (256 MiB write)",
-                      "weno_face_fraction": weno_frac, "t_start": t_dev, "t_after": t64},
+                      "weno_face_fraction": weno_frac, "t_start": t_dev, "t_after": t64,
+                      "tiles_autotuned": tiles},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk, "ms_per_step_all": ms64}
     res.update(extra)

@@ -164,6 +164,20 @@ weno_status weno_enqueue_steps(weno_ctx* ctx, double t_end, int nsteps);
 weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t flush_bytes, double* ms,
                              unsigned long long* weno_faces);
 
+/* Tile autotuner (no counterpart in the paper): for every sweep direction,
+ * times each compiled tile shape (lines x cells per CTA: 2x63, 8x15, 4x31)
+ * `reps` times on the current state and keeps the fastest for this
+ * context; variants[3] (if not NULL) receives the choice per direction.
+ * The state is not changed; the step graphs are rebuilt on next use.
+ * Synchronizes. */
+weno_status weno_autotune(weno_ctx* ctx, int reps, int* variants);
+
+/* Pin the tile shape of every sweep direction (variants[d] in 0..2, see
+ * weno_autotune; ignored in 1D).  Results do not depend on the tile shape:
+ * every face is computed by the same arithmetic.  WENO_ERR_INVALID_ARG for
+ * an unknown variant. */
+weno_status weno_set_tiles(weno_ctx* ctx, const int* variants);
+
 /* Conserved totals sum_cells U dV per variable (nvar doubles, host memory),
  * accumulated in double.  Synchronizes. */
 weno_status weno_conserved_totals(weno_ctx* ctx, double* totals);

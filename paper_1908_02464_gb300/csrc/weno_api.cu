@@ -48,6 +48,7 @@ struct weno_ctx {
     double* totals_dev = nullptr;
     int tot_blocks = 1;
     int phase = 0;
+    int tile[3] = {0, 0, 0};    // sweep tile variant per direction
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     bool graphs_ready = false;
     std::string err;
@@ -69,9 +70,10 @@ static size_t interior_cells(const weno_ctx* c) { return (size_t)c->n[0] * c->n[
 // ----------------------------------------------------------- dispatch
 static cudaError_t do_sweep(weno_ctx* c, int dir, const wis::SweepArgs& a, cudaStream_t s)
 {
-    if (c->prec == WENO_FP64) return wis::sweep_f64(c->dim, dir, a, s);
-    if (c->prec == WENO_FP32) return wis::sweep_f32(c->dim, dir, a, s);
-    return wis::sweep_mixed(c->dim, dir, a, s);
+    const int v = c->tile[dir];
+    if (c->prec == WENO_FP64) return wis::sweep_f64(c->dim, dir, v, a, s);
+    if (c->prec == WENO_FP32) return wis::sweep_f32(c->dim, dir, v, a, s);
+    return wis::sweep_mixed(c->dim, dir, v, a, s);
 }
 static cudaError_t do_ghost(weno_ctx* c, const wis::GhostArgs& a, cudaStream_t s)
 {
@@ -101,7 +103,20 @@ static wis::SweepArgs sweep_args(weno_ctx* c, int dir)
     a.c_lambda = c->p.c_lambda;
     a.hybrid = c->p.hybrid;
     a.weno_count = c->wcount;
+    a.inv_dx_f = (float)a.inv_dx;
+    a.gamma_f = (float)a.gamma;
+    a.eps_f = (float)a.eps;
+    a.lim0_f = (float)(3600.0 * a.eps_h);
+    a.lam_scale_f = (float)(a.c_lambda * (1.0 / 3600.0));
     return a;
+}
+
+static void set_rk(wis::SweepArgs& a, double ra, double rb)
+{
+    a.rk_a = ra;
+    a.rk_b = rb;
+    a.rk_a_f = (float)ra;
+    a.rk_b_f = (float)rb;
 }
 
 static wis::GhostArgs ghost_args(weno_ctx* c, void* U, int dir)
@@ -141,8 +156,7 @@ static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* ou
             a.Un = base;
             a.out = out;
             a.acc = c->dim > 1 ? c->acc : nullptr;
-            a.rk_a = ra;
-            a.rk_b = rb;
+            set_rk(a, ra, rb);
         } else {
             a.mode = d == 0 ? wis::MODE_ACC_SET : wis::MODE_ACC_ADD;
             a.acc = c->acc;
@@ -333,6 +347,9 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
         return WENO_ERR_CUDA;
     }
     std::memset(ctx->tm_host, 0, sizeof(DevTime));
+    // default tiles: long tiles in FP64 (ALU bound); coalesced rows for the
+    // float y/z sweeps
+    for (int d = 1; d < dim; ++d) ctx->tile[d] = ctx->prec == WENO_FP64 ? 0 : 1;
     *out = ctx;
     return WENO_OK;
 }
@@ -541,53 +558,123 @@ weno_status weno_enqueue_steps(weno_ctx* ctx, double t_end, int nsteps)
     return WENO_OK;
 }
 
-weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t flush_bytes, double* ms,
-                             unsigned long long* weno_faces)
+// mean event time of `reps` launches of the direction-d sweep (ACC_SET on the
+// current state, ghosts already filled); weno faces of one launch to *wf
+static weno_status time_sweep_dir(weno_ctx* ctx, int d, int reps, void* flush_dev, size_t flush_bytes,
+                                  cudaEvent_t e0, cudaEvent_t e1, double* ms, unsigned long long* wf)
 {
-    if (!ctx || reps < 1 || !ms) return WENO_ERR_INVALID_ARG;
+    void* cur = ctx->buf[ctx->phase];
+    double tot = 0.0;
+    for (int r = 0; r < reps; ++r) {
+        if (flush_dev && flush_bytes) CK(cudaMemsetAsync(flush_dev, r & 0xff, flush_bytes, ctx->stream));
+        CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
+        wis::SweepArgs a = sweep_args(ctx, d);
+        a.U = cur;
+        a.mode = wis::MODE_ACC_SET;
+        a.acc = ctx->dim > 1 ? ctx->acc : ctx->rhs_out;
+        CK(cudaEventRecord(e0, ctx->stream));
+        CK(do_sweep(ctx, d, a, ctx->stream));
+        CK(cudaEventRecord(e1, ctx->stream));
+        unsigned long long c = 0;
+        CK(cudaMemcpyAsync(&c, ctx->wcount, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        float m = 0.f;
+        CK(cudaEventElapsedTime(&m, e0, e1));
+        tot += m;
+        if (wf) *wf = c;
+    }
+    *ms = tot / reps;
+    return WENO_OK;
+}
+
+static weno_status prepare_timing(weno_ctx* ctx)
+{
     weno_status st = read_time(ctx);
     if (st != WENO_OK) return st;
+    if (ctx->dim == 1 && (st = ensure_rhs_bufs(ctx)) != WENO_OK) return st;
     void* cur = ctx->buf[ctx->phase];
     for (int d = 0; d < ctx->dim; ++d) {
         wis::GhostArgs ga = ghost_args(ctx, cur, d);
         ga.t_fixed = ctx->tm_host->t;
         CK(do_ghost(ctx, ga, ctx->stream));
     }
+    return WENO_OK;
+}
+
+weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t flush_bytes, double* ms,
+                             unsigned long long* weno_faces)
+{
+    if (!ctx || reps < 1 || !ms) return WENO_ERR_INVALID_ARG;
+    weno_status st = prepare_timing(ctx);
+    if (st != WENO_OK) return st;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int d = 0; d < ctx->dim; ++d) {
-        double tot = 0.0;
+    for (int d = 0; d < ctx->dim && st == WENO_OK; ++d) {
         unsigned long long wf = 0;
-        for (int r = 0; r < reps; ++r) {
-            if (flush_dev && flush_bytes) CK(cudaMemsetAsync(flush_dev, r & 0xff, flush_bytes, ctx->stream));
-            CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
-            wis::SweepArgs a = sweep_args(ctx, d);
-            a.U = cur;
-            a.mode = wis::MODE_ACC_SET;
-            a.acc = ctx->dim > 1 ? ctx->acc : ctx->rhs_out;
-            if (!a.acc) {
-                st = ensure_rhs_bufs(ctx);
-                if (st != WENO_OK) return st;
-                a.acc = ctx->rhs_out;
-            }
-            CK(cudaEventRecord(e0, ctx->stream));
-            CK(do_sweep(ctx, d, a, ctx->stream));
-            CK(cudaEventRecord(e1, ctx->stream));
-            unsigned long long c = 0;
-            CK(cudaMemcpyAsync(&c, ctx->wcount, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaEventSynchronize(e1));
-            CK(cudaStreamSynchronize(ctx->stream));
-            float m = 0.f;
-            CK(cudaEventElapsedTime(&m, e0, e1));
-            tot += m;
-            wf = c;
-        }
-        ms[d] = tot / reps;
+        st = time_sweep_dir(ctx, d, reps, flush_dev, flush_bytes, e0, e1, &ms[d], &wf);
         if (weno_faces) weno_faces[d] = wf;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (st != WENO_OK) return st;
+    CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return WENO_OK;
+}
+
+weno_status weno_set_tiles(weno_ctx* ctx, const int* variants)
+{
+    if (!ctx || !variants) return WENO_ERR_INVALID_ARG;
+    for (int d = 0; d < ctx->dim; ++d)
+        if (variants[d] < 0 || variants[d] >= wis::kTileVariants) return WENO_ERR_INVALID_ARG;
+    for (int d = 0; d < ctx->dim; ++d) ctx->tile[d] = ctx->dim == 1 ? 0 : variants[d];
+    for (int k = 0; k < 3; ++k) {
+        if (ctx->graph[k]) cudaGraphExecDestroy(ctx->graph[k]);
+        ctx->graph[k] = nullptr;
+    }
+    ctx->graphs_ready = false;
+    return WENO_OK;
+}
+
+weno_status weno_autotune(weno_ctx* ctx, int reps, int* variants)
+{
+    if (!ctx || reps < 1) return WENO_ERR_INVALID_ARG;
+    weno_status st = prepare_timing(ctx);
+    if (st != WENO_OK) return st;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int d = 0; d < ctx->dim && st == WENO_OK; ++d) {
+        if (ctx->dim == 1) break;   // one tile shape in 1D
+        const int keep = ctx->tile[d];
+        double best_ms[wis::kTileVariants];
+        for (int v = 0; v < wis::kTileVariants; ++v) best_ms[v] = 1e30;
+        // interleaved rounds, minimum per variant (robust to drift and noise)
+        for (int r = 0; r <= reps && st == WENO_OK; ++r) {
+            for (int v = 0; v < wis::kTileVariants && st == WENO_OK; ++v) {
+                ctx->tile[d] = v;
+                double m = 0.0;
+                st = time_sweep_dir(ctx, d, 1, nullptr, 0, e0, e1, &m, nullptr);
+                if (r > 0 && m < best_ms[v]) best_ms[v] = m;   // round 0 warms up
+            }
+        }
+        int best = keep;
+        for (int v = 0; v < wis::kTileVariants; ++v)
+            if (best_ms[v] < best_ms[best]) best = v;
+        ctx->tile[d] = st == WENO_OK ? best : keep;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != WENO_OK) return st;
+    if (variants)
+        for (int d = 0; d < 3; ++d) variants[d] = d < ctx->dim ? ctx->tile[d] : 0;
+    // the step graphs bake the kernel choice: rebuild them on next use
+    for (int k = 0; k < 3; ++k) {
+        if (ctx->graph[k]) cudaGraphExecDestroy(ctx->graph[k]);
+        ctx->graph[k] = nullptr;
+    }
+    ctx->graphs_ready = false;
     CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return WENO_OK;

@@ -52,52 +52,51 @@ template <> struct Ar<float> {
 
 // ------------------------------------------------------------- cell records
 // Per-cell quantities kept in shared memory for a sweep along direction DIR.
-// Record layout (NQ entries): U[NV], F[NV], u[DIM], H, sqrt(rho),
-// |u_n - c|, |u_n|, |u_n + c|.
+// Record layout (NQ entries): U[NV], F[NV], sqrt(rho) u[DIM], sqrt(rho) H,
+// sqrt(rho), |u_n - c|, |u_n|, |u_n + c|.  The sqrt(rho)-weighted velocity
+// and enthalpy make the Roe average of a face two sums and one scaling.
 template <int DIM> struct CellLayout {
     static constexpr int NV = DIM + 2;
     static constexpr int U = 0;
     static constexpr int F = NV;
-    static constexpr int VEL = 2 * NV;
-    static constexpr int H = 2 * NV + DIM;
-    static constexpr int SQ = H + 1;
-    static constexpr int LM = H + 2;   // |u_n - c|
-    static constexpr int L0 = H + 3;   // |u_n|
-    static constexpr int LP = H + 4;   // |u_n + c|
-    static constexpr int NQ = H + 5;
+    static constexpr int SU = 2 * NV;
+    static constexpr int SH = 2 * NV + DIM;
+    static constexpr int SQ = SH + 1;
+    static constexpr int LM = SH + 2;   // |u_n - c|
+    static constexpr int L0 = SH + 3;   // |u_n|
+    static constexpr int LP = SH + 4;   // |u_n + c|
+    static constexpr int NQ = SH + 5;
 };
 
-// Primitives, physical flux along DIR and |eigenvalues| of one cell.
-// q[k] receives record entry k (see CellLayout).
+// Primitives, physical flux along DIR and |eigenvalues| of one cell
+// (Eq. goveq4; E = p/(gamma-1) + rho |u|^2/2).  q[k] receives record entry k.
 template <typename T, int DIM, int DIR>
 __device__ __forceinline__ void cell_prepare(const T* U, T gamma, T* q)
 {
     using CL = CellLayout<DIM>;
     const T gm1 = gamma - T(1);
     const T rho = U[0];
-    const T irho = Ar<T>::rcp(rho);
-    T vel[DIM];
-    T ke2 = T(0);  // rho |u|^2
+    const T isq = Ar<T>::rsqrt_(rho);   // 1/sqrt(rho)
+    const T irho = isq * isq;
+    T m2 = T(0);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) {
-        vel[k] = U[1 + k] * irho;
-        ke2 = fmaT(U[1 + k], vel[k], ke2);
-    }
+    for (int k = 0; k < DIM; ++k) m2 = fmaT(U[1 + k], U[1 + k], m2);
     const T E = U[DIM + 1];
-    const T p = gm1 * fmaT(T(-0.5), ke2, E);
+    const T p = gm1 * fmaT(T(-0.5) * irho, m2, E);
     const T c = Ar<T>::sqrt_(gamma * p * irho);
-    const T un = vel[DIR];
+    const T un = U[1 + DIR] * irho;
+    const T Ep = E + p;
 #pragma unroll
     for (int v = 0; v < CL::NV; ++v) q[CL::U + v] = U[v];
     q[CL::F + 0] = U[1 + DIR];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) q[CL::F + 1 + k] = U[1 + k] * un;
     q[CL::F + 1 + DIR] += p;
-    q[CL::F + DIM + 1] = (E + p) * un;
+    q[CL::F + DIM + 1] = Ep * un;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) q[CL::VEL + k] = vel[k];
-    q[CL::H] = (E + p) * irho;
-    q[CL::SQ] = Ar<T>::sqrt_(rho);
+    for (int k = 0; k < DIM; ++k) q[CL::SU + k] = U[1 + k] * isq;
+    q[CL::SH] = Ep * isq;
+    q[CL::SQ] = rho * isq;
     q[CL::LM] = absT(un - c);
     q[CL::L0] = absT(un);
     q[CL::LP] = absT(un + c);
@@ -112,8 +111,8 @@ template <typename T, int DIM> struct Roe {
     T rt;        // Roe density sqrt(rho_a rho_b)
 };
 
-// Roe average between the cells whose records start at qa (j) and qb (j+1);
-// get(q, k) reads record entry k.
+// Roe average (Sec. 2.4 step (1)) between cells a (j) and b (j+1); get_a(k)
+// and get_b(k) read record entry k of the two cells.
 template <typename T, int DIM, typename GA, typename GB>
 __device__ __forceinline__ Roe<T, DIM> roe_state(GA get_a, GB get_b, T gamma)
 {
@@ -121,14 +120,13 @@ __device__ __forceinline__ Roe<T, DIM> roe_state(GA get_a, GB get_b, T gamma)
     Roe<T, DIM> r;
     const T sa = get_a(CL::SQ), sb = get_b(CL::SQ);
     const T inv = Ar<T>::rcp(sa + sb);
-    const T wa = sa * inv, wb = sb * inv;
     T q2 = T(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-        r.u[k] = fmaT(wa, get_a(CL::VEL + k), wb * get_b(CL::VEL + k));
+        r.u[k] = (get_a(CL::SU + k) + get_b(CL::SU + k)) * inv;
         q2 = fmaT(r.u[k], r.u[k], q2);
     }
-    r.H = fmaT(wa, get_a(CL::H), wb * get_b(CL::H));
+    r.H = (get_a(CL::SH) + get_b(CL::SH)) * inv;
     r.hq2 = T(0.5) * q2;
     const T gm1 = gamma - T(1);
     const T c2 = gm1 * (r.H - r.hq2);
@@ -138,6 +136,19 @@ __device__ __forceinline__ Roe<T, DIM> roe_state(GA get_a, GB get_b, T gamma)
     r.rt = sa * sb;
     return r;
 }
+
+// Order-preserving comparisons and maxima of non-negative values through
+// their IEEE bit patterns (integer pipe instead of the floating-point pipe).
+__device__ __forceinline__ double max_nn(double a, double b)
+{
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+__device__ __forceinline__ float max_nn(float a, float b)
+{
+    return __int_as_float(max(__float_as_int(a), __float_as_int(b)));
+}
+__device__ __forceinline__ bool lt_nn(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+__device__ __forceinline__ bool lt_nn(float a, float b) { return __float_as_int(a) < __float_as_int(b); }
 
 // w[s] = L^s . x for all fields.
 template <typename T, int DIM, int DIR>

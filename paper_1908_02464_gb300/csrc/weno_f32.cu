@@ -4,9 +4,9 @@
 
 namespace wis {
 
-cudaError_t sweep_f32(int dim, int dir, const SweepArgs& a, cudaStream_t s)
+cudaError_t sweep_f32(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s)
 {
-    return launch_sweep_t<float, false>(dim, dir, a, s);
+    return launch_sweep_t<float, false>(dim, dir, variant, a, s);
 }
 cudaError_t ghost_f32(int dim, const GhostArgs& a, cudaStream_t s) { return launch_ghost_t<float>(dim, a, s); }
 cudaError_t cfl_f32(int dim, const CflArgs& a, int nsm, cudaStream_t s) { return launch_cfl_t<float>(dim, a, nsm, s); }

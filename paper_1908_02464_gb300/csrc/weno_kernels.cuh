@@ -49,11 +49,18 @@ struct SweepArgs {
     long long sy, sz, sv, off0;
     double inv_dx, eps_h, gamma, eps, c_lambda;
     int hybrid;
+    // the same constants pre-rounded for float kernels (a double conversion
+    // or division per thread would run on the slow FP64 pipe)
+    float inv_dx_f, gamma_f, eps_f, lim0_f, lam_scale_f, rk_a_f, rk_b_f;
 };
+
+template <typename T> __device__ __forceinline__ T pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
 template <typename T, int DIM>
 struct FaceRec {
-    // face record kept for queued WENO faces: Roe state, detector, speeds
+    // record of a queued WENO face: Roe state, lambda^s, LLF speeds
     static constexpr int NV = DIM + 2;
     static constexpr int U = 0;               // u[DIM]
     static constexpr int C = DIM;
@@ -61,13 +68,15 @@ struct FaceRec {
     static constexpr int H = DIM + 2;
     static constexpr int B1 = DIM + 3;
     static constexpr int HQ2 = DIM + 4;
-    static constexpr int RT = DIM + 5;
-    static constexpr int W = DIM + 6;         // dv[NV]
-    static constexpr int AM = W + NV;         // alpha^{u-c}
+    static constexpr int LAM = DIM + 5;       // lambda^s = c (dv^s / rho~)^2, NV entries
+    static constexpr int AM = LAM + NV;       // alpha^{u-c}
     static constexpr int A0 = AM + 1;         // alpha^{u}, shear
     static constexpr int AP = AM + 2;         // alpha^{u+c}
     static constexpr int NR = AM + 3;
 };
+
+// WENO faces are processed in chunks of QC queued faces.
+template <int DIM> struct Chunk { static constexpr int QC = 16; };
 
 template <typename T, int DIM, int LINES, int SEG>
 struct SweepSmem {
@@ -78,13 +87,31 @@ struct SweepSmem {
     static constexpr int NQ = CellLayout<DIM>::NQ;
     static constexpr int NV = DIM + 2;
     static constexpr int NR = FaceRec<T, DIM>::NR;
+    static constexpr int QC = Chunk<DIM>::QC;
     static constexpr size_t bytes =
-        sizeof(T) * ((size_t)NQ * NCELL + (size_t)NV * NFACE + (size_t)NR * NFACE) +
+        sizeof(T) * ((size_t)NQ * NCELL + (size_t)NV * NFACE + (size_t)NR * NFACE +
+                     (size_t)QC * NV * 2 * 6 + (size_t)QC * NV * 2) +
         sizeof(int) * (size_t)NFACE;
 };
 
-template <typename T, int DIM, int DIR, int LINES, int SEG, int NT, bool DET64>
-__global__ void __launch_bounds__(NT) k_sweep(SweepArgs a)
+// -f_{j-2} + 5 f_{j-1} - 10 f_j + 10 f_{j+1} - 5 f_{j+2} + f_{j+3} as nested
+// differences (the negated detector combination of Eq. eq28).  In smooth
+// data consecutive differences are close, so each subtraction is exact
+// (Sterbenz): the float result carries no cancellation error.
+template <typename T>
+__device__ __forceinline__ T fifth_difference(T u0, T u1, T u2, T u3, T u4, T u5)
+{
+    T a0 = u1 - u0, a1 = u2 - u1, a2 = u3 - u2, a3 = u4 - u3, a4 = u5 - u4;
+    T b0 = a1 - a0, b1 = a2 - a1, b2 = a3 - a2, b3 = a4 - a3;
+    T c0 = b1 - b0, c1 = b2 - b1, c2 = b3 - b2;
+    T d0 = c1 - c0, d1 = c2 - c1;
+    return d1 - d0;
+}
+
+// EXACTDET: detector difference by nested differences (mixed precision);
+// otherwise the direct six-term combination.
+template <typename T, int DIM, int DIR, int LINES, int SEG, int NT, bool EXACTDET>
+__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
 {
     using CL = CellLayout<DIM>;
     using FR = FaceRec<T, DIM>;
@@ -94,16 +121,19 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a)
     constexpr int CELLS = SM::CELLS, FACES = SM::FACES;
     constexpr int NCELL = SM::NCELL, NFACE = SM::NFACE;
     constexpr int NR = FR::NR;
+    constexpr int QC = SM::QC;
 
     if (a.tm != nullptr) {
         if (a.tm->status != 0 || !(a.tm->dt > 0.0)) return;
     }
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* cq = reinterpret_cast<T*>(smem_raw);     // [NQ][NCELL]
-    T* fh = cq + NQ * NCELL;                    // [NV][NFACE]
-    T* fr = fh + NV * NFACE;                    // [NR][NFACE]
-    int* queue = reinterpret_cast<int*>(fr + NR * NFACE);
+    T* cq = reinterpret_cast<T*>(smem_raw);     // [NQ][NCELL]  cell records
+    T* fh = cq + NQ * NCELL;                    // [NV][NFACE]  face fluxes
+    T* fr = fh + NV * NFACE;                    // [NR][NFACE]  WENO face records
+    T* fpm = fr + NR * NFACE;                   // [QC][NV][2][6] split fluxes f+-
+    T* res = fpm + QC * NV * 2 * 6;             // [QC][NV][2]  reconstructions
+    int* queue = reinterpret_cast<int*>(res + QC * NV * 2);
     __shared__ int qcount;
     __shared__ unsigned int wcount;
 
@@ -117,7 +147,7 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a)
     const long long sd = DIR == 0 ? 1LL : (DIR == 1 ? a.sy : a.sz);
     const long long sl = DIR == 0 ? a.sy : 1LL;
     const long long sp = DIR == 2 ? a.sy : a.sz;
-    const T gamma = T(a.gamma);
+    const T gamma = pick<T>(a.gamma, a.gamma_f);
 
     const T* Ug = reinterpret_cast<const T*>(a.U);
 
@@ -143,13 +173,18 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a)
     }
     __syncthreads();
 
+    // shared-memory order follows the global order: along-the-line for x
+    // sweeps, across the lines (x fastest) for y/z sweeps; consecutive
+    // threads read consecutive words in both cases
     auto cidx = [](int l, int p) -> int { return DIR == 0 ? l * CELLS + p : p * LINES + l; };
     auto fdec = [](int f, int& l, int& p) {
         if (DIR == 0) { l = f / FACES; p = f - l * FACES; }
         else { p = f / LINES; l = f - p * LINES; }
     };
 
-    const T eps_h = T(a.eps_h);
+    // sigma^s < eps_h  <=>  (60 dv^s)^2 < 3600 eps_h rho~^2
+    const T lim0 = pick<T>(3600.0 * a.eps_h, a.lim0_f);
+    const T lam_scale = pick<T>(a.c_lambda * (1.0 / 3600.0), a.lam_scale_f);
     const int lane = threadIdx.x & 31;
     unsigned int my_weno = 0;
 
@@ -167,51 +202,38 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a)
             auto ga = [&](int k) -> T { return cq[k * NCELL + cidx(l, p + 2)]; };
             auto gb = [&](int k) -> T { return cq[k * NCELL + cidx(l, p + 3)]; };
             const Roe<T, DIM> r = roe_state<T, DIM>(ga, gb, gamma);
-            // Eq. eq28: dU = (U_{j-2} + 10 U_j + 5 U_{j+2}) - (5 U_{j-1} + 10 U_{j+1} + U_{j+3})
+            // Eq. eq28 without the 1/60: w = L (U_{j-2} - 5U_{j-1} + 10U_j - 10U_{j+1} + 5U_{j+2} - U_{j+3})
             T dU[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 const int k = CL::U + v;
-                if (DET64) {
-                    const double u0 = (double)cq[k * NCELL + cidx(l, p + 0)];
-                    const double u1 = (double)cq[k * NCELL + cidx(l, p + 1)];
-                    const double u2 = (double)cq[k * NCELL + cidx(l, p + 2)];
-                    const double u3 = (double)cq[k * NCELL + cidx(l, p + 3)];
-                    const double u4 = (double)cq[k * NCELL + cidx(l, p + 4)];
-                    const double u5 = (double)cq[k * NCELL + cidx(l, p + 5)];
-                    dU[v] = (T)((u0 + fmaT(10.0, u2, 5.0 * u4)) - (u5 + fmaT(10.0, u3, 5.0 * u1)));
-                } else {
-                    const T u0 = cq[k * NCELL + cidx(l, p + 0)];
-                    const T u1 = cq[k * NCELL + cidx(l, p + 1)];
-                    const T u2 = cq[k * NCELL + cidx(l, p + 2)];
-                    const T u3 = cq[k * NCELL + cidx(l, p + 3)];
-                    const T u4 = cq[k * NCELL + cidx(l, p + 4)];
-                    const T u5 = cq[k * NCELL + cidx(l, p + 5)];
-                    dU[v] = (u0 + fmaT(T(10), u2, T(5) * u4)) - (u5 + fmaT(T(10), u3, T(5) * u1));
-                }
+                const T u0 = cq[k * NCELL + cidx(l, p + 0)];
+                const T u1 = cq[k * NCELL + cidx(l, p + 1)];
+                const T u2 = cq[k * NCELL + cidx(l, p + 2)];
+                const T u3 = cq[k * NCELL + cidx(l, p + 3)];
+                const T u4 = cq[k * NCELL + cidx(l, p + 4)];
+                const T u5 = cq[k * NCELL + cidx(l, p + 5)];
+                if (EXACTDET) dU[v] = -fifth_difference(u0, u1, u2, u3, u4, u5);
+                else dU[v] = fmaT(T(10), u2 - u3, fmaT(T(5), u4 - u1, u0 - u5));
             }
             T w[NV];
             proj_all<T, DIM, DIR>(r, dU, w);
-            // sigma^s = (dv^s / rho~)^2 < eps_h  <=>  dv^2 < eps_h rho~^2
-            const T lim = eps_h * (r.rt * r.rt);
+            const T lim = lim0 * (r.rt * r.rt);
             bool smooth = a.hybrid != 0;
 #pragma unroll
-            for (int s = 0; s < NV; ++s) {
-                w[s] *= T(1.0 / 60.0);
-                smooth = smooth && (w[s] * w[s] < lim);
-            }
+            for (int s = 0; s < NV; ++s) smooth = smooth && lt_nn(w[s] * w[s], lim);
             // LLF speeds: max over the six stencil cells
             T am = cq[CL::LM * NCELL + cidx(l, p)];
             T a0 = cq[CL::L0 * NCELL + cidx(l, p)];
             T ap = cq[CL::LP * NCELL + cidx(l, p)];
 #pragma unroll
             for (int m = 1; m < 6; ++m) {
-                am = maxT(am, cq[CL::LM * NCELL + cidx(l, p + m)]);
-                a0 = maxT(a0, cq[CL::L0 * NCELL + cidx(l, p + m)]);
-                ap = maxT(ap, cq[CL::LP * NCELL + cidx(l, p + m)]);
+                am = max_nn(am, cq[CL::LM * NCELL + cidx(l, p + m)]);
+                a0 = max_nn(a0, cq[CL::L0 * NCELL + cidx(l, p + m)]);
+                ap = max_nn(ap, cq[CL::LP * NCELL + cidx(l, p + m)]);
             }
             if (smooth) {
-                // Eq. linearupwind: central six-point flux plus sum_s R^s alpha^s dv^s
+                // Eq. linearupwind: [central six-point flux + sum_s R^s alpha^s (60 dv^s)] / 60
                 T Fo[NV];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
@@ -219,7 +241,7 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a)
                     const T f05 = cq[k * NCELL + cidx(l, p + 0)] + cq[k * NCELL + cidx(l, p + 5)];
                     const T f14 = cq[k * NCELL + cidx(l, p + 1)] + cq[k * NCELL + cidx(l, p + 4)];
                     const T f23 = cq[k * NCELL + cidx(l, p + 2)] + cq[k * NCELL + cidx(l, p + 3)];
-                    Fo[v] = fmaT(T(37), f23, fmaT(T(-8), f14, f05)) * T(1.0 / 60.0);
+                    Fo[v] = fmaT(T(37), f23, fmaT(T(-8), f14, f05));
                 }
                 T aw[NV];
                 aw[0] = am * w[0];
@@ -228,7 +250,7 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a)
                 aw[NV - 1] = ap * w[NV - 1];
                 back_proj_add<T, DIM, DIR>(r, aw, Fo);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = Fo[v];
+                for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = Fo[v] * T(1.0 / 60.0);
             } else {
                 weno = true;
 #pragma unroll
@@ -238,9 +260,10 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a)
                 fr[FR::H * NFACE + f] = r.H;
                 fr[FR::B1 * NFACE + f] = r.b1;
                 fr[FR::HQ2 * NFACE + f] = r.hq2;
-                fr[FR::RT * NFACE + f] = r.rt;
+                // Eq. eq27, eq29: lambda^s = c (dv^s / rho~)^2 = c w_s^2 / (3600 rho~^2)
+                const T irt2 = Ar<T>::rcp(r.rt * r.rt);
 #pragma unroll
-                for (int s = 0; s < NV; ++s) fr[(FR::W + s) * NFACE + f] = w[s];
+                for (int s = 0; s < NV; ++s) fr[(FR::LAM + s) * NFACE + f] = lam_scale * (w[s] * w[s]) * irt2;
                 fr[FR::AM * NFACE + f] = am;
                 fr[FR::A0 * NFACE + f] = a0;
                 fr[FR::AP * NFACE + f] = ap;
@@ -274,113 +297,90 @@ __global__ void __launch_bounds__(NT) k_sweep(SweepArgs a)
 
     // ---- phase 2: characteristic regularized WENO-IS flux of queued faces --
     const int nq = qcount;
-    const T eps = T(a.eps), clam = T(a.c_lambda);
-    for (int qi = threadIdx.x; qi < nq; qi += NT) {
-        const int f = queue[qi];
-        int l, p;
-        fdec(f, l, p);
-        Roe<T, DIM> r;
+    const T eps = pick<T>(a.eps, a.eps_f);
+    for (int q0 = 0; q0 < nq; q0 += QC) {
+        const int qc = nq - q0 < QC ? nq - q0 : QC;
+        // 2a: project U_m and F_m of the six stencil cells (Eq. eqchara) and
+        //     split them (Eq. flxuspliting); one work item per (face, cell)
+        for (int it = threadIdx.x; it < qc * 6; it += NT) {
+            const int q = it / 6, m = it - (it / 6) * 6;
+            const int f = queue[q0 + q];
+            int l, p;
+            fdec(f, l, p);
+            Roe<T, DIM> r;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) r.u[k] = fr[(FR::U + k) * NFACE + f];
-        r.c = fr[FR::C * NFACE + f];
-        r.ic = fr[FR::IC * NFACE + f];
-        r.H = fr[FR::H * NFACE + f];
-        r.b1 = fr[FR::B1 * NFACE + f];
-        r.hq2 = fr[FR::HQ2 * NFACE + f];
-        r.rt = fr[FR::RT * NFACE + f];
-        const T irt = Ar<T>::rcp(r.rt);
-        const T am = fr[FR::AM * NFACE + f];
-        const T a0 = fr[FR::A0 * NFACE + f];
-        const T ap = fr[FR::AP * NFACE + f];
-
-        // shared parts of the projections (Eq. eqchara) of U_m and F_m, m = j-2..j+3
-        T t1U[6], aU[6], t1F[6], aF[6];
-#pragma unroll
-        for (int m = 0; m < 6; ++m) {
+            for (int k = 0; k < DIM; ++k) r.u[k] = fr[(FR::U + k) * NFACE + f];
+            r.ic = fr[FR::IC * NFACE + f];
+            r.b1 = fr[FR::B1 * NFACE + f];
+            r.hq2 = fr[FR::HQ2 * NFACE + f];
+            const T am = fr[FR::AM * NFACE + f];
+            const T a0 = fr[FR::A0 * NFACE + f];
+            const T ap = fr[FR::AP * NFACE + f];
             const int ci = cidx(l, p + m);
-            T xu[NV], xf[NV];
+            T xu[NV], xf[NV], wv[NV], wg[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 xu[v] = cq[(CL::U + v) * NCELL + ci];
                 xf[v] = cq[(CL::F + v) * NCELL + ci];
             }
-            T du = r.u[0] * xu[1], df = r.u[0] * xf[1];
+            proj_all<T, DIM, DIR>(r, xu, wv);
+            proj_all<T, DIM, DIR>(r, xf, wg);
 #pragma unroll
-            for (int k = 1; k < DIM; ++k) { du = fmaT(r.u[k], xu[1 + k], du); df = fmaT(r.u[k], xf[1 + k], df); }
-            t1U[m] = r.b1 * (fmaT(r.hq2, xu[0], xu[DIM + 1]) - du);
-            t1F[m] = r.b1 * (fmaT(r.hq2, xf[0], xf[DIM + 1]) - df);
-            aU[m] = fmaT(r.u[DIR], xu[0], -xu[1 + DIR]) * r.ic;
-            aF[m] = fmaT(r.u[DIR], xf[0], -xf[1 + DIR]) * r.ic;
-        }
-
-        T wch[NV];
-#pragma unroll
-        for (int s = 0; s < NV; ++s) {
-            T vv[6], gg[6];
-            T alpha;
-            if (s == 0) {
-                alpha = am;
-#pragma unroll
-                for (int m = 0; m < 6; ++m) { vv[m] = T(0.5) * (t1U[m] + aU[m]); gg[m] = T(0.5) * (t1F[m] + aF[m]); }
-            } else if (s == 1) {
-                alpha = a0;
-#pragma unroll
-                for (int m = 0; m < 6; ++m) {
-                    const int ci = cidx(l, p + m);
-                    vv[m] = cq[CL::U * NCELL + ci] - t1U[m];
-                    gg[m] = cq[CL::F * NCELL + ci] - t1F[m];
-                }
-            } else if (s == NV - 1) {
-                alpha = ap;
-#pragma unroll
-                for (int m = 0; m < 6; ++m) { vv[m] = T(0.5) * (t1U[m] - aU[m]); gg[m] = T(0.5) * (t1F[m] - aF[m]); }
-            } else {
-                // shear field s -> tangential direction t (skipping DIR)
-                alpha = a0;
-                int t = s - 2;
-                if (t >= DIR) ++t;
-                const T ut = r.u[t];
-#pragma unroll
-                for (int m = 0; m < 6; ++m) {
-                    const int ci = cidx(l, p + m);
-                    vv[m] = fmaT(-ut, cq[CL::U * NCELL + ci], cq[(CL::U + 1 + t) * NCELL + ci]);
-                    gg[m] = fmaT(-ut, cq[CL::F * NCELL + ci], cq[(CL::F + 1 + t) * NCELL + ci]);
-                }
+            for (int s = 0; s < NV; ++s) {
+                const T al = s == 0 ? am : (s == NV - 1 ? ap : a0);
+                const T h = T(0.5) * wg[s];
+                const T k = T(0.5) * al * wv[s];
+                fpm[((q * NV + s) * 2 + 0) * 6 + m] = h + k;
+                fpm[((q * NV + s) * 2 + 1) * 6 + m] = h - k;
             }
-            // Eq. flxuspliting: f^{+-} = (g +- alpha v)/2
-            T fp[6], fm[6];
-#pragma unroll
-            for (int m = 0; m < 6; ++m) {
-                const T h = T(0.5) * gg[m];
-                const T k = T(0.5) * alpha * vv[m];
-                fp[m] = h + k;
-                fm[m] = h - k;
-            }
-            // Eq. eq27, eq29: lambda = c (dv / rho~)^2
-            const T dvr = fr[(FR::W + s) * NFACE + f] * irt;
-            const T lam = clam * (dvr * dvr);
-            // Eq. reconstruction: + on j-2..j+2, - on the mirrored j+3..j-1
-            const T fplus = recon<T>(fp[0], fp[1], fp[2], fp[3], fp[4], lam, eps);
-            const T fminus = recon<T>(fm[5], fm[4], fm[3], fm[2], fm[1], lam, eps);
-            wch[s] = fplus + fminus;   // Eq. reconstruction1
         }
-        T Fo[NV];
+        __syncthreads();
+        // 2b: one reconstruction per (face, field, sign): Eq. eq6, eq11, eq18,
+        //     eq8-r; the minus part on the mirrored stencil j+3 .. j-1
+        for (int it = threadIdx.x; it < qc * NV * 2; it += NT) {
+            const int q = it / (2 * NV);
+            const int rem = it - q * (2 * NV);
+            const int s = rem >> 1, sg = rem & 1;
+            const int f = queue[q0 + q];
+            const T lam = fr[(FR::LAM + s) * NFACE + f];
+            const T* v = fpm + ((q * NV + s) * 2 + sg) * 6;
+            T out;
+            if (sg == 0) out = recon<T>(v[0], v[1], v[2], v[3], v[4], lam, eps);
+            else out = recon<T>(v[5], v[4], v[3], v[2], v[1], lam, eps);
+            res[(q * NV + s) * 2 + sg] = out;
+        }
+        __syncthreads();
+        // 2c: Eq. reconstruction1 and the back-projection Eq. reconstruction2
+        for (int q = threadIdx.x; q < qc; q += NT) {
+            const int f = queue[q0 + q];
+            Roe<T, DIM> r;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) Fo[v] = T(0);
-        back_proj_add<T, DIM, DIR>(r, wch, Fo);   // Eq. reconstruction2
+            for (int k = 0; k < DIM; ++k) r.u[k] = fr[(FR::U + k) * NFACE + f];
+            r.c = fr[FR::C * NFACE + f];
+            r.H = fr[FR::H * NFACE + f];
+            r.hq2 = fr[FR::HQ2 * NFACE + f];
+            T wch[NV], Fo[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = Fo[v];
+            for (int s = 0; s < NV; ++s) {
+                wch[s] = res[(q * NV + s) * 2] + res[(q * NV + s) * 2 + 1];
+                Fo[s] = T(0);
+            }
+            back_proj_add<T, DIM, DIR>(r, wch, Fo);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = Fo[v];
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0 && a.weno_count != nullptr && wcount != 0u)
         atomicAdd(a.weno_count, (unsigned long long)wcount);
 
     // ---- flux divergence and output ---------------------------------------
-    const T inv_dx = T(a.inv_dx);
+    const T inv_dx = pick<T>(a.inv_dx, a.inv_dx_f);
     T* outp = reinterpret_cast<T*>(a.out);
     T* accp = reinterpret_cast<T*>(a.acc);
     const T* Unp = reinterpret_cast<const T*>(a.Un);
-    T dt = T(0), rka = T(a.rk_a), rkb = T(a.rk_b);
+    T dt = T(0);
+    const T rka = pick<T>(a.rk_a, a.rk_a_f), rkb = pick<T>(a.rk_b, a.rk_b_f);
     if (a.mode == MODE_COMBINE) dt = T(a.tm->dt);
     bool bad = false;
     for (int idx = threadIdx.x; idx < LINES * SEG; idx += NT) {

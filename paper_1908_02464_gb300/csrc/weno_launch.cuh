@@ -10,26 +10,32 @@
 
 namespace wis {
 
-// Tile shapes.  x-sweeps take LINES rows of SEG contiguous cells; y/z sweeps
-// take 32 consecutive x-columns (one coalesced 32-element row per cell
-// position) of SEG cells along the sweep.
-template <int DIM, int DIR> struct Tile;
-template <> struct Tile<1, 0> { static constexpr int LINES = 1, SEG = 128, NT = 128; };
-template <> struct Tile<2, 0> { static constexpr int LINES = 4, SEG = 64, NT = 256; };
-template <> struct Tile<2, 1> { static constexpr int LINES = 32, SEG = 8, NT = 256; };
-template <> struct Tile<3, 0> { static constexpr int LINES = 4, SEG = 64, NT = 256; };
-template <> struct Tile<3, 1> { static constexpr int LINES = 32, SEG = 8, NT = 256; };
-template <> struct Tile<3, 2> { static constexpr int LINES = 32, SEG = 8, NT = 256; };
+// Tile shapes: LINES grid lines of SEG cells along the sweep (plus a 3-cell
+// halo on each side).  LINES x (SEG + 1) faces equal the CTA size, so the
+// face phase runs in exactly one round (on the FP64 pipe a partly filled
+// warp costs as much as a full one).  Variants:
+//   0 long   2 x 63  halo work ~10%; y/z loads are 2-element row pieces
+//   1 wide   8 x 15  8-element rows (coalesced y/z loads), halo work 40%
+//   2 medium 4 x 31
+// FP64 is ALU bound (variant 0 everywhere); FP32 y/z sweeps prefer coalesced
+// rows.  weno_autotune times the variants on a live state and keeps the best.
+constexpr int kTileVariants = 3;
+template <int V> struct Tile;
+template <> struct Tile<0> { static constexpr int LINES = 2, SEG = 63, NT = 128; };
+template <> struct Tile<1> { static constexpr int LINES = 8, SEG = 15, NT = 128; };
+template <> struct Tile<2> { static constexpr int LINES = 4, SEG = 31, NT = 128; };
+struct Tile1D { static constexpr int LINES = 1, SEG = 127, NT = 128; };
 
-template <typename T, int DIM, int DIR, bool DET64>
+template <typename T, int DIM, int DIR, bool EXACTDET, typename TL>
 cudaError_t launch_sweep_one(const SweepArgs& a, cudaStream_t s)
 {
-    using TL = Tile<DIM, DIR>;
     using SM = SweepSmem<T, DIM, TL::LINES, TL::SEG>;
-    auto kern = k_sweep<T, DIM, DIR, TL::LINES, TL::SEG, TL::NT, DET64>;
+    auto kern = k_sweep<T, DIM, DIR, TL::LINES, TL::SEG, TL::NT, EXACTDET>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         configured = true;
     }
@@ -43,17 +49,25 @@ cudaError_t launch_sweep_one(const SweepArgs& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-template <typename T, bool DET64>
-cudaError_t launch_sweep_t(int dim, int dir, const SweepArgs& a, cudaStream_t s)
+template <typename T, int DIM, int DIR, bool EXACTDET>
+cudaError_t launch_sweep_v(int variant, const SweepArgs& a, cudaStream_t s)
 {
-    if (dim == 1) return launch_sweep_one<T, 1, 0, DET64>(a, s);
+    if (variant == 1) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<1>>(a, s);
+    if (variant == 2) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<2>>(a, s);
+    return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<0>>(a, s);
+}
+
+template <typename T, bool EXACTDET>
+cudaError_t launch_sweep_t(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s)
+{
+    if (dim == 1) return launch_sweep_one<T, 1, 0, EXACTDET, Tile1D>(a, s);
     if (dim == 2) {
-        if (dir == 0) return launch_sweep_one<T, 2, 0, DET64>(a, s);
-        return launch_sweep_one<T, 2, 1, DET64>(a, s);
+        if (dir == 0) return launch_sweep_v<T, 2, 0, EXACTDET>(variant, a, s);
+        return launch_sweep_v<T, 2, 1, EXACTDET>(variant, a, s);
     }
-    if (dir == 0) return launch_sweep_one<T, 3, 0, DET64>(a, s);
-    if (dir == 1) return launch_sweep_one<T, 3, 1, DET64>(a, s);
-    return launch_sweep_one<T, 3, 2, DET64>(a, s);
+    if (dir == 0) return launch_sweep_v<T, 3, 0, EXACTDET>(variant, a, s);
+    if (dir == 1) return launch_sweep_v<T, 3, 1, EXACTDET>(variant, a, s);
+    return launch_sweep_v<T, 3, 2, EXACTDET>(variant, a, s);
 }
 
 inline int grid_for(long long work, int threads, int cap)
@@ -110,9 +124,9 @@ cudaError_t launch_pack_t(const void* src, void* dst, int nv, const int* n, long
 }
 
 // per-precision entry points (one translation unit each)
-cudaError_t sweep_f64(int dim, int dir, const SweepArgs& a, cudaStream_t s);
-cudaError_t sweep_f32(int dim, int dir, const SweepArgs& a, cudaStream_t s);
-cudaError_t sweep_mixed(int dim, int dir, const SweepArgs& a, cudaStream_t s);
+cudaError_t sweep_f64(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);
+cudaError_t sweep_f32(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);
+cudaError_t sweep_mixed(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);
 cudaError_t ghost_f64(int dim, const GhostArgs& a, cudaStream_t s);
 cudaError_t ghost_f32(int dim, const GhostArgs& a, cudaStream_t s);
 cudaError_t cfl_f64(int dim, const CflArgs& a, int nsm, cudaStream_t s);

@@ -1,13 +1,13 @@
-// Mixed instantiations: float storage and bulk arithmetic; the fifth
+// Mixed instantiations: float storage and arithmetic, with the fifth
 // difference of the detector (Eq. eq28), whose cancellation decides the
-// hybrid switch, is formed in double.
+// hybrid switch, formed as exact nested float differences.
 #include "weno_launch.cuh"
 
 namespace wis {
 
-cudaError_t sweep_mixed(int dim, int dir, const SweepArgs& a, cudaStream_t s)
+cudaError_t sweep_mixed(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s)
 {
-    return launch_sweep_t<float, true>(dim, dir, a, s);
+    return launch_sweep_t<float, true>(dim, dir, variant, a, s);
 }
 
 }  // namespace wis

@@ -64,6 +64,8 @@ SIGNATURES = {
     "weno_last_error": (ctypes.c_char_p, [_vp]),
     "weno_measure_fma_peak": (ctypes.c_int, [_ip, _dp, _dp]),
     "weno_enqueue_steps": (ctypes.c_int, [_vp, ctypes.c_double, _ip]),
+    "weno_autotune": (ctypes.c_int, [_vp, _ip, ctypes.POINTER(_ip)]),
+    "weno_set_tiles": (ctypes.c_int, [_vp, ctypes.POINTER(_ip)]),
     "weno_conserved_totals_noalloc": (ctypes.c_int, [_ip, ctypes.POINTER(_ip), _dp, _ip, _vp, _vp, _vp]),
     "weno_time_sweeps": (ctypes.c_int, [_vp, _ip, _vp, ctypes.c_size_t, _dp, ctypes.POINTER(ctypes.c_ulonglong)]),
 }
@@ -193,6 +195,17 @@ def weno_conserved_totals_noalloc(dim: int, n, dx, precision: str, U_dev, totals
     dd = (ctypes.c_double * 3)(*(list(dx) + [1.0] * (3 - len(dx))))
     _check(load().weno_conserved_totals_noalloc(int(dim), nn, dd, PRECISIONS[precision], _vp(_ptr(U_dev)),
                                                 _vp(_ptr(totals_dev)), _vp(stream or None)))
+
+
+def weno_autotune(ctx: int, reps: int = 3):
+    v = (ctypes.c_int * 3)()
+    _check(load().weno_autotune(_vp(ctx), int(reps), v), _vp(ctx))
+    return list(v)
+
+
+def weno_set_tiles(ctx: int, variants) -> None:
+    v = (ctypes.c_int * 3)(*(list(variants) + [0] * (3 - len(variants))))
+    _check(load().weno_set_tiles(_vp(ctx), v), _vp(ctx))
 
 
 def weno_enqueue_steps(ctx: int, t_end: float, nsteps: int) -> None:
@@ -328,6 +341,12 @@ class Solver:
 
     def enqueue_steps(self, t_end: float, nsteps: int):
         weno_enqueue_steps(self.ctx, t_end, nsteps)
+
+    def set_tiles(self, variants):
+        weno_set_tiles(self.ctx, variants)
+
+    def autotune(self, reps: int = 3):
+        return weno_autotune(self.ctx, reps)[:self.dim]
 
     def time_sweeps(self, reps: int = 5, flush=None):
         return weno_time_sweeps(self.ctx, self.dim, reps, flush)

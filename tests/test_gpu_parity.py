@@ -215,6 +215,38 @@ def test_step_equals_advance_bitwise():
     assert np.array_equal(A, B)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tile_variants_give_bitwise_identical_results(precision):
+    """Every face is computed by the same arithmetic whatever the tiling."""
+    for dim, n in ((2, [150, 37]), (3, [40, 23, 19])):
+        prob, U = P.random_state(dim, n, seed=77, kind="mixed")
+        outs = []
+        for v in range(3):
+            s = weno.Solver(prob, precision)
+            s.set_tiles([v] * dim)
+            Ud = torch.from_numpy(U).cuda()
+            outs.append(s.rhs(Ud).cpu().numpy())
+            s.set_state(U)
+            s.advance(1.0, max_steps=3)
+            outs.append(s.get_state()[0])
+            s.close()
+        for k in range(2, len(outs)):
+            assert np.array_equal(outs[k], outs[k % 2])
+
+
+def test_autotune_keeps_state_and_results():
+    prob, U = P.double_mach(256, 64)
+    s = weno.Solver(prob, "fp64")
+    s.set_state(U)
+    s.advance(0.002)
+    V0, t0 = s.get_state()
+    v = s.autotune(2)
+    assert all(0 <= x < 3 for x in v)
+    V1, t1 = s.get_state()
+    assert t1 == t0 and np.array_equal(V0, V1)
+    s.close()
+
+
 def test_totals_match_oracle_and_are_conserved():
     prob, U = P.random_state(2, [48, 40], seed=9, kind="mixed")
     s = weno.Solver(prob)
