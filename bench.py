@@ -259,6 +259,8 @@ def run_ours(args) -> dict:
            "api": "weno_set_state(host) + weno_step + weno_get_state(host)"}
     s64.close()
 
+    batch = None if args.no_batch else batched_riemann(args)
+
     launches_per_step = 3 + 3 * 2 * 2 + 1   # cfl, dt, post, 3 x (2 ghosts + 2 sweeps), set_tend
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
@@ -272,11 +274,55 @@ def run_ours(args) -> dict:
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk, "ms_per_step_all": ms64}
     res.update(extra)
+    if batch is not None:
+        res["batched_riemann"] = batch
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return res if rank == 0 else None
+
+
+def batched_riemann(args) -> dict:
+    """4096 random 1D Riemann problems (N ~ U[100, 4000]) solved to their own
+    end times by one persistent, graph-replayed launch per precision."""
+    import torch
+    from paper_1908_02464_gb300 import problems as P
+    from paper_1908_02464_gb300 import weno
+    params, redraws = P.riemann_batch_params(args.batch_count, seed=20190807)
+    states = [P.riemann_instance(params, i)[1] for i in range(args.batch_count)]
+    out = {"instances": args.batch_count, "cells": int(params["N"].sum()), "redraws": redraws,
+           "workload": "random Riemann problems on [0,1], rho and p log-uniform in [0.01, 10], u in [-2, 2], "
+                       "N ~ U[100, 4000], t_end = 0.2 / max(|u|+c), seed 20190807, transmissive"}
+    ref = None
+    for prec in ("fp64", "fp32", "mixed"):
+        b = weno.Batch(params["N"], 0.0, 1.0, params["t_end"], prec)
+        U0 = b.pack(states)
+        U = U0.clone()
+        choice = b.autotune(U, trial_steps=3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run(U)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st, steps, t = b.results()
+        cu = 3.0 * float(np.sum(params["N"] * steps))
+        entry = {"value": cu / (ms * 1e-3), "unit": UNIT, "seconds": ms * 1e-3, "cell_updates": cu,
+                 "nonphysical_instances": int(np.sum(st != 0)), "tile_variant": choice[0], "ctas": choice[1],
+                 "steps_total": int(steps.sum())}
+        res = b.unpack(U)
+        if prec == "fp64":
+            ref = res
+        else:
+            ok = [i for i in range(b.count) if st[i] == 0]
+            l1 = [float(np.mean(np.abs(res[i][0] - ref[i][0]))) for i in ok]
+            entry["l1_rho_vs_fp64_mean"] = float(np.mean(l1))
+            entry["l1_rho_vs_fp64_max"] = float(np.max(l1))
+        out[prec] = entry
+        b.close()
+    return out
 
 
 # ---------------------------------------------------------------- oracle arm
@@ -333,6 +379,8 @@ def main():
     ap.add_argument("--fp64-only", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep-reps", type=int, default=5)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=4096)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -182,6 +182,62 @@ weno_status weno_set_tiles(weno_ctx* ctx, const int* variants);
  * accumulated in double.  Synchronizes. */
 weno_status weno_conserved_totals(weno_ctx* ctx, double* totals);
 
+/* ------------------------------------------------------------------------
+ * Batched 1D problems (many independent shock tubes of uneven sizes).
+ * Each instance i is a 1D Euler problem on [lo[i], hi[i]] with n[i] cells,
+ * advanced from t = 0 to t_end[i] with its own CFL step (same scheme and
+ * constants as weno_params), in one persistent launch replayed from a CUDA
+ * graph: every CTA takes the next instance from a work queue ordered
+ * largest first and runs its whole RK3 loop (Sec. 4) on its own.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int count;              /* number of instances (>= 1)                      */
+    const int* n;           /* host [count]: cells of each instance (>= 3)     */
+    const double* lo;       /* host [count]                                    */
+    const double* hi;       /* host [count]                                    */
+    const double* t_end;    /* host [count]: end time of each instance         */
+    int bc_lo, bc_hi;       /* WENO_BC_TRANSMISSIVE, _REFLECT or _PERIODIC     */
+    int max_steps;          /* per-instance step limit, 0 = none               */
+} weno_batch_desc;
+
+typedef struct weno_batch weno_batch;
+
+/* Create a batch: copies the description, orders the instances largest
+ * first, allocates three ghosted work arrays per instance.  States are passed
+ * to weno_batch_run as one device array holding the instances back to back,
+ * instance i as [3][n[i]] (rho, rho u, E) starting at element 3 sum_{j<i} n[j]
+ * (double for WENO_FP64, float otherwise).  Errors: WENO_ERR_INVALID_ARG for
+ * an empty batch, n < 3, hi <= lo, negative t_end, other boundary codes or an
+ * unknown precision; WENO_ERR_CUDA if allocation fails. */
+weno_status weno_batch_create(const weno_batch_desc* desc, const weno_params* params, void* stream,
+                              weno_batch** out);
+
+/* Advance every instance of U_dev (in place: initial states in, states at
+ * their t_end out) in one graph-replayed persistent launch.  Asynchronous;
+ * read the per-instance outcome with weno_batch_results. */
+weno_status weno_batch_run(weno_batch* batch, void* U_dev);
+
+/* Per-instance results of the last run (host arrays of count entries, each
+ * may be NULL): status (0 ok, WENO_ERR_NONPHYSICAL: the instance stopped at
+ * its last admissible step), completed steps and reached time.
+ * Synchronizes; returns WENO_ERR_NONPHYSICAL if any instance failed. */
+weno_status weno_batch_results(weno_batch* batch, int* status, long long* steps, double* t);
+
+/* Autotuner (no counterpart in the paper): times trial runs of trial_steps
+ * steps per instance on U_dev (not modified) for each CTA size (64, 128, 256
+ * threads: tiles of 63, 127, 255 faces) and residency (all that fit, 4 or 2
+ * CTAs per SM) and keeps the fastest.  choice[0] = tile variant, choice[1] =
+ * CTAs launched.  Synchronizes. */
+weno_status weno_batch_autotune(weno_batch* batch, const void* U_dev, int trial_steps, int* choice);
+
+void weno_batch_destroy(weno_batch* batch);
+const char* weno_batch_last_error(const weno_batch* batch);
+
+/* One-call form: create, run, collect per-instance status (host array of
+ * count ints, may be NULL), destroy. */
+weno_status weno_batch_solve(const weno_batch_desc* desc, const weno_params* params, void* stream, void* U_dev,
+                             int* per_instance);
+
 /* Allocation-free conserved totals (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory where they need
  * the totals: code running while a stream is being captured into a CUDA

@@ -1,0 +1,541 @@
+// Batched 1D solver: many independent Euler problems of uneven sizes, each
+// advanced to its own end time with its own CFL step, in one persistent
+// launch replayed from a CUDA graph.
+//
+// Each CTA pulls an instance from a work queue (instances ordered largest
+// first, so the tail of the schedule holds the small ones), copies it into
+// three ghosted work arrays that stay L2-resident while it is being solved,
+// and runs the whole RK3 loop (Sec. 4 of the paper) with block-level
+// barriers only: CFL max-reduction, then per stage the ghost cells and a
+// chain of sweep tiles (the same per-tile code as the grid solver, so every
+// face is computed by identical arithmetic).  No CTA ever waits on another.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/weno_is.h"
+#include "weno_kernels.cuh"
+
+namespace wis {
+
+struct BatchArgs {
+    int count;
+    const int* order;        // instance ids, largest first
+    const int* n;            // cells per instance
+    const long long* off;    // offset of instance i in U ([3][n_i] interior)
+    const long long* goff;   // offset of instance i in each work array ([3][n_i + 6])
+    const double* dx;
+    const double* t_end;
+    void* U;
+    void* work0;
+    void* work1;
+    void* work2;
+    int* status;             // per instance: 0 ok, WENO_ERR_NONPHYSICAL
+    long long* steps;
+    double* t_out;
+    unsigned int* head;      // work-queue counter (reset before each launch)
+    unsigned long long* weno_count;
+    int max_steps;
+    int write_back;          // 0: trial run, the caller's states are not touched
+    double gamma, cfl, eps, c_lambda, C_thr, L_char;
+    int alpha_thr, hybrid, bc_lo, bc_hi;
+};
+
+template <int V> struct BatchTile;
+template <> struct BatchTile<0> { static constexpr int SEG = 127, NT = 128; };
+template <> struct BatchTile<1> { static constexpr int SEG = 63, NT = 64; };
+template <> struct BatchTile<2> { static constexpr int SEG = 255, NT = 256; };
+constexpr int kBatchVariants = 3;
+
+template <typename T, int NT>
+__device__ __forceinline__ void batch_ghosts(T* W, int n, long long sv, int bc_lo, int bc_hi)
+{
+    // three ghost layers per side, 1D: transmissive, reflecting or periodic
+    if (threadIdx.x < 6) {
+        const int side = threadIdx.x / 3, gl = threadIdx.x % 3 + 1;
+        const int bc = side == 0 ? bc_lo : bc_hi;
+        const int dst = side == 0 ? -gl : n - 1 + gl;
+        int src;
+        if (bc == BC_TRANSMISSIVE) src = side == 0 ? 0 : n - 1;
+        else if (bc == BC_REFLECT) src = side == 0 ? gl - 1 : n - gl;
+        else src = side == 0 ? n - gl : gl - 1;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            T val = W[3 + v * sv + src];
+            if (bc == BC_REFLECT && v == 1) val = -val;
+            W[3 + v * sv + dst] = val;
+        }
+    }
+}
+
+template <typename T, int SEG, int NT, bool EXACTDET>
+__global__ void __launch_bounds__(NT) k_batch(BatchArgs b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_inst;
+    __shared__ double s_red[NT / 32];
+    __shared__ double s_dt;
+    __shared__ int s_flag;
+    const T gamma = T(b.gamma);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned int k = atomicAdd(b.head, 1u);
+            s_inst = k < (unsigned int)b.count ? b.order[k] : -1;
+        }
+        __syncthreads();
+        const int inst = s_inst;
+        if (inst < 0) return;
+        const int n = b.n[inst];
+        const long long sv = n + 6;
+        T* W[3] = {reinterpret_cast<T*>(b.work0) + b.goff[inst], reinterpret_cast<T*>(b.work1) + b.goff[inst],
+                   reinterpret_cast<T*>(b.work2) + b.goff[inst]};
+        T* Ui = reinterpret_cast<T*>(b.U) + b.off[inst];
+        for (int i = threadIdx.x; i < n; i += NT)
+#pragma unroll
+            for (int v = 0; v < 3; ++v) W[0][3 + v * sv + i] = Ui[(long long)v * n + i];
+        const double dx = b.dx[inst], t_end = b.t_end[inst];
+        // Eq. eq31
+        double eps_h = b.C_thr;
+        for (int k = 0; k < b.alpha_thr; ++k) eps_h *= dx / b.L_char;
+
+        SweepArgs a;
+        a.acc = nullptr;
+        a.mode = MODE_COMBINE;
+        a.tm = nullptr;
+        a.weno_count = b.weno_count;
+        a.flags = nullptr;
+        a.n[0] = n; a.n[1] = 1; a.n[2] = 1;
+        a.sy = sv; a.sz = sv; a.sv = sv; a.off0 = 3;
+        a.inv_dx = 1.0 / dx;
+        a.eps_h = eps_h;
+        a.gamma = b.gamma; a.eps = b.eps; a.c_lambda = b.c_lambda; a.hybrid = b.hybrid;
+        a.inv_dx_f = (float)a.inv_dx; a.gamma_f = (float)b.gamma; a.eps_f = (float)b.eps;
+        a.lim0_f = (float)(3600.0 * eps_h); a.lam_scale_f = (float)(b.c_lambda * (1.0 / 3600.0));
+        const T inv_dx_t[1] = {T(a.inv_dx)};
+        const int ntiles = (n + SEG - 1) / SEG;
+
+        int cur = 0, x = 1, y = 2;
+        double t = 0.0;
+        long long steps = 0;
+        int status = 0;
+        __syncthreads();
+        while (steps < b.max_steps) {
+            // CFL max-reduction (same per-cell arithmetic as the grid solver)
+            double smax = 0.0;
+            bool bad = false;
+            for (int i = threadIdx.x; i < n; i += NT) {
+                T u[3];
+#pragma unroll
+                for (int v = 0; v < 3; ++v) u[v] = W[cur][3 + v * sv + i];
+                T s;
+                if (!cell_speed<T, 1>(u, gamma, inv_dx_t, s)) bad = true;
+                else smax = maxT(smax, (double)s);
+            }
+            smax = warp_max(smax);
+            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = smax;
+            const int anybad = __syncthreads_or(bad);
+            if (threadIdx.x == 0) {
+                double m = 0.0;
+                for (int w = 0; w < NT / 32; ++w) m = maxT(m, s_red[w]);
+                int clipped = 0;
+                s_dt = anybad ? 0.0 : cfl_step(b.cfl, m, t, t_end, &clipped);
+                s_flag = clipped;
+            }
+            __syncthreads();
+            const double dt = s_dt;
+            const int clipped = s_flag;
+            if (anybad) { status = WENO_ERR_NONPHYSICAL; break; }
+            if (!(dt > 0.0)) break;
+            const T dtt = T(dt);
+            // three stages: x = cur + dt L(cur); y = 3/4 cur + 1/4 (x + dt L(x));
+            // x = 1/3 cur + 2/3 (y + dt L(y))
+            const int in_[3] = {cur, x, y}, out_[3] = {x, y, x};
+            const double ra[3] = {0.0, 0.75, 1.0 / 3.0}, rb[3] = {1.0, 0.25, 2.0 / 3.0};
+            bool sbad = false;
+            for (int st = 0; st < 3; ++st) {
+                batch_ghosts<T, NT>(W[in_[st]], n, sv, b.bc_lo, b.bc_hi);
+                __syncthreads();
+                a.U = W[in_[st]];
+                a.Un = W[cur];
+                a.out = W[out_[st]];
+                a.rk_a = ra[st]; a.rk_b = rb[st];
+                a.rk_a_f = (float)ra[st]; a.rk_b_f = (float)rb[st];
+                for (int tile = 0; tile < ntiles; ++tile)
+                    sbad |= sweep_tile<T, 1, 0, 1, SEG, NT, EXACTDET>(a, tile, 0, 0, dtt, smem_raw);
+            }
+            if (__syncthreads_or(sbad)) { status = WENO_ERR_NONPHYSICAL; break; }
+            const int tmp = cur;
+            cur = x;
+            x = tmp;
+            t = clipped ? t_end : t + dt;
+            ++steps;
+        }
+        if (b.write_back)
+            for (int i = threadIdx.x; i < n; i += NT)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) Ui[(long long)v * n + i] = W[cur][3 + v * sv + i];
+        if (threadIdx.x == 0) {
+            b.status[inst] = status;
+            b.steps[inst] = steps;
+            b.t_out[inst] = t;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, bool EXACTDET, int V>
+cudaError_t batch_config(int* blocks_per_sm, size_t* smem)
+{
+    using BT = BatchTile<V>;
+    using SM = SweepSmem<T, 1, 1, BT::SEG>;
+    auto kern = k_batch<T, BT::SEG, BT::NT, EXACTDET>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    *smem = SM::bytes;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, BT::NT, SM::bytes);
+}
+
+template <typename T, bool EXACTDET, int V>
+cudaError_t batch_launch(const BatchArgs& b, int blocks, cudaStream_t s)
+{
+    using BT = BatchTile<V>;
+    using SM = SweepSmem<T, 1, 1, BT::SEG>;
+    k_batch<T, BT::SEG, BT::NT, EXACTDET><<<blocks, BT::NT, SM::bytes, s>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace wis
+
+using wis::BatchArgs;
+
+struct weno_batch {
+    int count = 0, prec = 0, dev = 0, nsm = 1;
+    size_t esz = 8;
+    weno_params p;
+    int bc_lo = 0, bc_hi = 0, max_steps = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    long long total_cells = 0, total_ghosted = 0;
+    int* order = nullptr;
+    int* n = nullptr;
+    long long* off = nullptr;
+    long long* goff = nullptr;
+    double* dx = nullptr;
+    double* t_end = nullptr;
+    void* work[3] = {nullptr, nullptr, nullptr};
+    int* status = nullptr;
+    long long* steps = nullptr;
+    double* t_out = nullptr;
+    unsigned int* head = nullptr;
+    unsigned long long* wcount = nullptr;
+    int variant = 0;
+    int blocks = 0;
+    cudaGraphExec_t graph = nullptr;
+    void* graph_U = nullptr;
+    std::string err;
+};
+
+static std::string g_batch_err;
+
+#define BCK(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            bt->err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
+            return WENO_ERR_CUDA;                                                           \
+        }                                                                                   \
+    } while (0)
+
+static cudaError_t batch_dispatch_config(int prec, int v, int* bps, size_t* smem)
+{
+    using namespace wis;
+    if (prec == WENO_FP64) {
+        if (v == 1) return batch_config<double, false, 1>(bps, smem);
+        if (v == 2) return batch_config<double, false, 2>(bps, smem);
+        return batch_config<double, false, 0>(bps, smem);
+    }
+    const bool ex = prec == WENO_MIXED;
+    if (v == 1) return ex ? batch_config<float, true, 1>(bps, smem) : batch_config<float, false, 1>(bps, smem);
+    if (v == 2) return ex ? batch_config<float, true, 2>(bps, smem) : batch_config<float, false, 2>(bps, smem);
+    return ex ? batch_config<float, true, 0>(bps, smem) : batch_config<float, false, 0>(bps, smem);
+}
+
+static cudaError_t batch_dispatch_launch(int prec, int v, const BatchArgs& b, int blocks, cudaStream_t s)
+{
+    using namespace wis;
+    if (prec == WENO_FP64) {
+        if (v == 1) return batch_launch<double, false, 1>(b, blocks, s);
+        if (v == 2) return batch_launch<double, false, 2>(b, blocks, s);
+        return batch_launch<double, false, 0>(b, blocks, s);
+    }
+    const bool ex = prec == WENO_MIXED;
+    if (v == 1) return ex ? batch_launch<float, true, 1>(b, blocks, s) : batch_launch<float, false, 1>(b, blocks, s);
+    if (v == 2) return ex ? batch_launch<float, true, 2>(b, blocks, s) : batch_launch<float, false, 2>(b, blocks, s);
+    return ex ? batch_launch<float, true, 0>(b, blocks, s) : batch_launch<float, false, 0>(b, blocks, s);
+}
+
+static BatchArgs batch_args(weno_batch* bt, void* U, int max_steps, int write_back)
+{
+    BatchArgs b;
+    std::memset(&b, 0, sizeof(b));
+    b.count = bt->count;
+    b.order = bt->order; b.n = bt->n; b.off = bt->off; b.goff = bt->goff;
+    b.dx = bt->dx; b.t_end = bt->t_end;
+    b.U = U;
+    b.work0 = bt->work[0]; b.work1 = bt->work[1]; b.work2 = bt->work[2];
+    b.status = bt->status; b.steps = bt->steps; b.t_out = bt->t_out;
+    b.head = bt->head;
+    b.weno_count = bt->wcount;
+    b.max_steps = max_steps;
+    b.write_back = write_back;
+    b.gamma = bt->p.gamma; b.cfl = bt->p.cfl; b.eps = bt->p.eps; b.c_lambda = bt->p.c_lambda;
+    b.C_thr = bt->p.C_thr; b.L_char = bt->p.L_char; b.alpha_thr = bt->p.alpha_thr; b.hybrid = bt->p.hybrid;
+    b.bc_lo = bt->bc_lo; b.bc_hi = bt->bc_hi;
+    return b;
+}
+
+static weno_status set_variant(weno_batch* bt, int v, int blocks_per_sm_cap)
+{
+    int bps = 0;
+    size_t smem = 0;
+    BCK(batch_dispatch_config(bt->prec, v, &bps, &smem));
+    if (bps < 1) { bt->err = "batch kernel cannot be resident"; return WENO_ERR_CUDA; }
+    if (blocks_per_sm_cap > 0 && bps > blocks_per_sm_cap) bps = blocks_per_sm_cap;
+    bt->variant = v;
+    long long blocks = (long long)bps * bt->nsm;
+    if (blocks > bt->count) blocks = bt->count;
+    bt->blocks = (int)blocks;
+    if (bt->graph) cudaGraphExecDestroy(bt->graph);
+    bt->graph = nullptr;
+    return WENO_OK;
+}
+
+// reset the queue and launch once (on stream s, optionally under capture)
+static cudaError_t enqueue_run(weno_batch* bt, void* U, int max_steps, int write_back, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bt->head, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    BatchArgs b = batch_args(bt, U, max_steps, write_back);
+    return batch_dispatch_launch(bt->prec, bt->variant, b, bt->blocks, s);
+}
+
+static void batch_free(weno_batch* bt)
+{
+    if (bt->graph) cudaGraphExecDestroy(bt->graph);
+    void* ptrs[] = {bt->order, bt->n, bt->off, bt->goff, bt->dx, bt->t_end, bt->work[0], bt->work[1],
+                    bt->work[2], bt->status, bt->steps, bt->t_out, bt->head, bt->wcount};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (bt->cap) cudaStreamDestroy(bt->cap);
+}
+
+extern "C" {
+
+weno_status weno_batch_create(const weno_batch_desc* d, const weno_params* params, void* stream, weno_batch** out)
+{
+    if (out) *out = nullptr;
+    if (!d || !params || !out || d->count < 1 || !d->n || !d->lo || !d->hi || !d->t_end) {
+        g_batch_err = "invalid batch description";
+        return WENO_ERR_INVALID_ARG;
+    }
+    if (params->precision < WENO_FP64 || params->precision > WENO_MIXED || d->max_steps < 0) {
+        g_batch_err = "invalid precision or max_steps";
+        return WENO_ERR_INVALID_ARG;
+    }
+    for (int s = 0; s < 2; ++s) {
+        const int bc = s == 0 ? d->bc_lo : d->bc_hi;
+        if (bc != WENO_BC_TRANSMISSIVE && bc != WENO_BC_REFLECT && bc != WENO_BC_PERIODIC) {
+            g_batch_err = "batched problems take transmissive, reflecting or periodic boundaries";
+            return WENO_ERR_INVALID_ARG;
+        }
+    }
+    if ((d->bc_lo == WENO_BC_PERIODIC) != (d->bc_hi == WENO_BC_PERIODIC)) {
+        g_batch_err = "periodic boundaries must be paired";
+        return WENO_ERR_INVALID_ARG;
+    }
+    const int cnt = d->count;
+    std::vector<long long> off(cnt), goff(cnt);
+    std::vector<double> dx(cnt), tend(cnt);
+    long long tc = 0, tg = 0;
+    for (int i = 0; i < cnt; ++i) {
+        if (d->n[i] < 3 || !(d->hi[i] > d->lo[i]) || !(d->t_end[i] >= 0.0)) {
+            g_batch_err = "instance with n < 3, hi <= lo or negative t_end";
+            return WENO_ERR_INVALID_ARG;
+        }
+        off[i] = tc;
+        goff[i] = tg;
+        tc += 3LL * d->n[i];
+        tg += 3LL * (d->n[i] + 6);
+        dx[i] = (d->hi[i] - d->lo[i]) / d->n[i];
+        tend[i] = d->t_end[i];
+    }
+    // schedule: largest instances first
+    std::vector<int> order(cnt);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return d->n[a] > d->n[b]; });
+
+    weno_batch* bt = new (std::nothrow) weno_batch();
+    if (!bt) { g_batch_err = "out of host memory"; return WENO_ERR_CUDA; }
+    bt->count = cnt;
+    bt->p = *params;
+    bt->prec = params->precision;
+    bt->esz = bt->prec == WENO_FP64 ? sizeof(double) : sizeof(float);
+    bt->bc_lo = d->bc_lo;
+    bt->bc_hi = d->bc_hi;
+    bt->max_steps = d->max_steps > 0 ? d->max_steps : 0x7fffffff;
+    bt->stream = (cudaStream_t)stream;
+    bt->total_cells = tc / 3;
+    bt->total_ghosted = tg;
+    cudaError_t e = cudaGetDevice(&bt->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&bt->nsm, cudaDevAttrMultiProcessorCount, bt->dev);
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void**)&bt->order, sizeof(int) * cnt);
+    alloc((void**)&bt->n, sizeof(int) * cnt);
+    alloc((void**)&bt->off, sizeof(long long) * cnt);
+    alloc((void**)&bt->goff, sizeof(long long) * cnt);
+    alloc((void**)&bt->dx, sizeof(double) * cnt);
+    alloc((void**)&bt->t_end, sizeof(double) * cnt);
+    for (int k = 0; k < 3; ++k) alloc(&bt->work[k], bt->esz * (size_t)tg);
+    alloc((void**)&bt->status, sizeof(int) * cnt);
+    alloc((void**)&bt->steps, sizeof(long long) * cnt);
+    alloc((void**)&bt->t_out, sizeof(double) * cnt);
+    alloc((void**)&bt->head, sizeof(unsigned int));
+    alloc((void**)&bt->wcount, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(bt->order, order.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->n, d->n, sizeof(int) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->off, off.data(), sizeof(long long) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->goff, goff.data(), sizeof(long long) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->dx, dx.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->t_end, tend.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(bt->wcount, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        g_batch_err = std::string("weno_batch_create: ") + cudaGetErrorString(e);
+        batch_free(bt);
+        delete bt;
+        return WENO_ERR_CUDA;
+    }
+    weno_status st = set_variant(bt, 0, 0);
+    if (st != WENO_OK) {
+        g_batch_err = bt->err;
+        batch_free(bt);
+        delete bt;
+        return st;
+    }
+    *out = bt;
+    return WENO_OK;
+}
+
+void weno_batch_destroy(weno_batch* bt)
+{
+    if (!bt) return;
+    if (bt->stream) cudaStreamSynchronize(bt->stream);
+    else cudaDeviceSynchronize();
+    batch_free(bt);
+    delete bt;
+}
+
+const char* weno_batch_last_error(const weno_batch* bt) { return bt ? bt->err.c_str() : g_batch_err.c_str(); }
+
+weno_status weno_batch_run(weno_batch* bt, void* U_dev)
+{
+    if (!bt || !U_dev) return WENO_ERR_INVALID_ARG;
+    if (!bt->graph || bt->graph_U != U_dev) {
+        if (bt->graph) cudaGraphExecDestroy(bt->graph);
+        bt->graph = nullptr;
+        cudaGraph_t g = nullptr;
+        BCK(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeRelaxed));
+        cudaError_t e = enqueue_run(bt, U_dev, bt->max_steps, 1, bt->cap);
+        cudaError_t e2 = cudaStreamEndCapture(bt->cap, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            bt->err = std::string("batch graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+            return WENO_ERR_CUDA;
+        }
+        e = cudaGraphInstantiate(&bt->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            bt->err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+            return WENO_ERR_CUDA;
+        }
+        bt->graph_U = U_dev;
+    }
+    BCK(cudaGraphLaunch(bt->graph, bt->stream));
+    return WENO_OK;
+}
+
+weno_status weno_batch_results(weno_batch* bt, int* status, long long* steps, double* t)
+{
+    if (!bt) return WENO_ERR_INVALID_ARG;
+    if (status) BCK(cudaMemcpyAsync(status, bt->status, sizeof(int) * bt->count, cudaMemcpyDeviceToHost, bt->stream));
+    if (steps) BCK(cudaMemcpyAsync(steps, bt->steps, sizeof(long long) * bt->count, cudaMemcpyDeviceToHost, bt->stream));
+    if (t) BCK(cudaMemcpyAsync(t, bt->t_out, sizeof(double) * bt->count, cudaMemcpyDeviceToHost, bt->stream));
+    BCK(cudaStreamSynchronize(bt->stream));
+    if (status)
+        for (int i = 0; i < bt->count; ++i)
+            if (status[i] != WENO_OK) {
+                bt->err = "at least one instance reached a non-physical state";
+                return WENO_ERR_NONPHYSICAL;
+            }
+    return WENO_OK;
+}
+
+weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_steps, int* choice)
+{
+    if (!bt || !U_dev || trial_steps < 1) return WENO_ERR_INVALID_ARG;
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_v = bt->variant, best_cap = 0;
+    const int caps[3] = {0, 4, 2};   // 0 = as many CTAs per SM as fit
+    weno_status st = WENO_OK;
+    for (int v = 0; v < wis::kBatchVariants && st == WENO_OK; ++v) {
+        for (int c = 0; c < 3 && st == WENO_OK; ++c) {
+            st = set_variant(bt, v, caps[c]);
+            if (st != WENO_OK) break;
+            float ms = 1e30f;
+            for (int r = 0; r < 2; ++r) {   // first run loads the kernel
+                if (cudaEventRecord(e0, bt->stream) != cudaSuccess ||
+                    enqueue_run(bt, const_cast<void*>(U_dev), trial_steps, 0, bt->stream) != cudaSuccess ||
+                    cudaEventRecord(e1, bt->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    bt->err = "batch autotune launch failed";
+                    st = WENO_ERR_CUDA;
+                    break;
+                }
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (st == WENO_OK && ms < best) { best = ms; best_v = v; best_cap = caps[c]; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != WENO_OK) return st;
+    st = set_variant(bt, best_v, best_cap);
+    if (choice) { choice[0] = best_v; choice[1] = bt->blocks; }
+    return st;
+}
+
+weno_status weno_batch_solve(const weno_batch_desc* d, const weno_params* params, void* stream, void* U_dev,
+                             int* per_instance)
+{
+    weno_batch* bt = nullptr;
+    weno_status st = weno_batch_create(d, params, stream, &bt);
+    if (st != WENO_OK) return st;
+    st = weno_batch_run(bt, U_dev);
+    if (st == WENO_OK) st = weno_batch_results(bt, per_instance, nullptr, nullptr);
+    if (st != WENO_OK && st != WENO_ERR_NONPHYSICAL) g_batch_err = bt->err;
+    weno_batch_destroy(bt);
+    return st;
+}
+
+}  // extern "C"

@@ -108,10 +108,15 @@ __device__ __forceinline__ T fifth_difference(T u0, T u1, T u2, T u3, T u4, T u5
     return d1 - d0;
 }
 
+// One tile of the sweep: stage, faces, WENO queue, divergence and output.
 // EXACTDET: detector difference by nested differences (mixed precision);
-// otherwise the direct six-term combination.
+// otherwise the direct six-term combination.  dt is the RK step (COMBINE
+// mode only).  Returns true in every thread whose cells failed the
+// admissibility check.  Ends with a barrier, so tiles can be chained by one
+// CTA (the batched solver) reusing the same shared memory.
 template <typename T, int DIM, int DIR, int LINES, int SEG, int NT, bool EXACTDET>
-__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
+__device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int line0, int pb, T dt,
+                                           unsigned char* smem_raw)
 {
     using CL = CellLayout<DIM>;
     using FR = FaceRec<T, DIM>;
@@ -123,11 +128,6 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
     constexpr int NR = FR::NR;
     constexpr int QC = SM::QC;
 
-    if (a.tm != nullptr) {
-        if (a.tm->status != 0 || !(a.tm->dt > 0.0)) return;
-    }
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* cq = reinterpret_cast<T*>(smem_raw);     // [NQ][NCELL]  cell records
     T* fh = cq + NQ * NCELL;                    // [NV][NFACE]  face fluxes
     T* fr = fh + NV * NFACE;                    // [NR][NFACE]  WENO face records
@@ -137,10 +137,6 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
     __shared__ int qcount;
     __shared__ unsigned int wcount;
 
-    int seg_blk, line0, pb;
-    if (DIR == 0) { seg_blk = blockIdx.x; line0 = blockIdx.y * LINES; pb = blockIdx.z; }
-    else if (DIR == 1) { seg_blk = blockIdx.y; line0 = blockIdx.x * LINES; pb = blockIdx.z; }
-    else { seg_blk = blockIdx.z; line0 = blockIdx.x * LINES; pb = blockIdx.y; }
     const int nd = a.n[DIR];
     const int c0 = seg_blk * SEG;
     const int nline = (DIR == 0) ? a.n[1] : a.n[0];
@@ -379,9 +375,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
     T* outp = reinterpret_cast<T*>(a.out);
     T* accp = reinterpret_cast<T*>(a.acc);
     const T* Unp = reinterpret_cast<const T*>(a.Un);
-    T dt = T(0);
     const T rka = pick<T>(a.rk_a, a.rk_a_f), rkb = pick<T>(a.rk_b, a.rk_b_f);
-    if (a.mode == MODE_COMBINE) dt = T(a.tm->dt);
     bool bad = false;
     for (int idx = threadIdx.x; idx < LINES * SEG; idx += NT) {
         int l, p;
@@ -425,6 +419,23 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
             if (!(nu[0] > T(0)) || !(chk > T(0)) || !isfinite(chk)) bad = true;
         }
     }
+    __syncthreads();
+    return bad;
+}
+
+template <typename T, int DIM, int DIR, int LINES, int SEG, int NT, bool EXACTDET>
+__global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
+{
+    if (a.tm != nullptr) {
+        if (a.tm->status != 0 || !(a.tm->dt > 0.0)) return;
+    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int seg_blk, line0, pb;
+    if (DIR == 0) { seg_blk = blockIdx.x; line0 = blockIdx.y * LINES; pb = blockIdx.z; }
+    else if (DIR == 1) { seg_blk = blockIdx.y; line0 = blockIdx.x * LINES; pb = blockIdx.z; }
+    else { seg_blk = blockIdx.z; line0 = blockIdx.x * LINES; pb = blockIdx.y; }
+    const T dt = a.mode == MODE_COMBINE ? T(a.tm->dt) : T(0);
+    const bool bad = sweep_tile<T, DIM, DIR, LINES, SEG, NT, EXACTDET>(a, seg_blk, line0, pb, dt, smem_raw);
     if (bad) atomicOr(&a.tm->status, 1);
 }
 
@@ -526,6 +537,39 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
+// CFL wave-speed sum sum_d (|u_d| + c) / dx_d of one cell; false if the cell
+// is not admissible (rho <= 0, p <= 0 or non-finite).  Shared by the grid
+// reduction and the batched solver so both take identical time steps.
+template <typename T, int DIM>
+__device__ __forceinline__ bool cell_speed(const T* u, T gamma, const T* inv_dx, T& s)
+{
+    const T gm1 = gamma - T(1);
+    const T irho = Ar<T>::rcp(u[0]);
+    T ke2 = T(0);
+    T vel[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) { vel[d] = u[1 + d] * irho; ke2 = fmaT(u[1 + d], vel[d], ke2); }
+    const T p = gm1 * fmaT(T(-0.5), ke2, u[DIM + 1]);
+    const T c = Ar<T>::sqrt_(gamma * p * irho);
+    s = T(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) s = fmaT(absT(vel[d]) + c, inv_dx[d], s);
+    return (u[0] > T(0)) && (p > T(0)) && isfinite(s);
+}
+
+// dt = CFL / smax clipped to t_end (the clipped step lands exactly on t_end)
+__device__ __forceinline__ double cfl_step(double cfl, double smax, double t, double t_end, int* clipped)
+{
+    double dt = 0.0;
+    *clipped = 0;
+    if (t < t_end) {
+        if (smax > 0.0) dt = cfl / smax;
+        if (t + dt >= t_end) { dt = t_end - t; *clipped = 1; }
+        if (!(dt > 0.0)) { dt = 0.0; *clipped = 0; }
+    }
+    return dt;
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_cfl(CflArgs a)
 {
@@ -534,7 +578,7 @@ __global__ void __launch_bounds__(256) k_cfl(CflArgs a)
     const T* U = reinterpret_cast<const T*>(a.U);
     const long long nx = a.n[0], ny = a.n[1];
     const long long total = nx * ny * (long long)a.n[2];
-    const T gamma = T(a.gamma), gm1 = gamma - T(1);
+    const T gamma = T(a.gamma);
     T idx_[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) idx_[k] = T(a.inv_dx[k]);
@@ -547,17 +591,8 @@ __global__ void __launch_bounds__(256) k_cfl(CflArgs a)
         T u[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) u[v] = U[g + v * a.sv];
-        const T irho = Ar<T>::rcp(u[0]);
-        T ke2 = T(0);
-        T vel[DIM];
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) { vel[d] = u[1 + d] * irho; ke2 = fmaT(u[1 + d], vel[d], ke2); }
-        const T p = gm1 * fmaT(T(-0.5), ke2, u[DIM + 1]);
-        const T c = Ar<T>::sqrt_(gamma * p * irho);
-        T s = T(0);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) s = fmaT(absT(vel[d]) + c, idx_[d], s);
-        if (!(u[0] > T(0)) || !(p > T(0)) || !isfinite(s)) bad = true;
+        T s;
+        if (!cell_speed<T, DIM>(u, gamma, idx_, s)) bad = true;
         else smax = maxT(smax, (double)s);
     }
     __shared__ double red[8];
@@ -579,11 +614,9 @@ static __global__ void k_dt(DevTime* tm, double cfl)
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double dt = 0.0;
     int clipped = 0;
-    if (tm->status == 0 && tm->t < tm->t_end) {
+    if (tm->status == 0) {
         const double smax = __longlong_as_double((long long)tm->smax_bits);
-        if (smax > 0.0) dt = cfl / smax;
-        if (tm->t + dt >= tm->t_end) { dt = tm->t_end - tm->t; clipped = 1; }
-        if (!(dt > 0.0)) { dt = 0.0; clipped = 0; }
+        dt = cfl_step(cfl, smax, tm->t, tm->t_end, &clipped);
     }
     tm->dt = dt;
     tm->clipped = clipped;

@@ -210,9 +210,13 @@ def riemann_batch_params(count: int = 4096, seed: int = 20190807, gamma: float =
     """Random 1D Riemann problems on [0, 1] with the interface at 0.5.
 
     N ~ U{n_lo..n_hi}; rho, p log-uniform in [0.01, 10] per side; u ~ U[-2, 2].
-    Draws whose two rarefactions would come within a factor two of the
-    vacuum condition 2(c_L + c_R)/(gamma - 1) <= u_R - u_L are redrawn from
-    the same stream.  t_end = 0.2 / max(|u_L| + c_L, |u_R| + c_R).
+    Draws are redrawn from the same stream when the data generate a vacuum
+    (2(c_L + c_R)/(gamma - 1) <= u_R - u_L, here with a factor-two margin) or
+    a star pressure below 1e-3 min(p_L, p_R).  A star pressure below
+    min(p_L, p_R) means two rarefactions, for which the closed form
+    p* = [(c_L + c_R - (gamma-1)(u_R - u_L)/2) / (c_L p_L^-z + c_R p_R^-z)]^(1/z),
+    z = (gamma-1)/(2 gamma), is exact, so the test needs no iteration.
+    t_end = 0.2 / max(|u_L| + c_L, |u_R| + c_R).
     Returns a dict of arrays (N, WL[count,3], WR[count,3], t_end) and the
     number of redraws."""
     rng = np.random.Generator(np.random.Philox(seed))
@@ -226,6 +230,12 @@ def riemann_batch_params(count: int = 4096, seed: int = 20190807, gamma: float =
         ul, ur = rng.uniform(-2.0, 2.0, size=2)
         cl = math.sqrt(gamma * pl / rl); cr = math.sqrt(gamma * pr / rr)
         if 2.0 * (cl + cr) / (gamma - 1.0) <= 2.0 * (ur - ul):
+            redraws += 1
+            continue
+        z = (gamma - 1.0) / (2.0 * gamma)
+        num = cl + cr - 0.5 * (gamma - 1.0) * (ur - ul)
+        p_tr = (num / (cl * pl ** (-z) + cr * pr ** (-z))) ** (1.0 / z)
+        if p_tr < 1e-3 * min(pl, pr):
             redraws += 1
             continue
         N[i] = n; WL[i] = (rl, ul, pl); WR[i] = (rr, ur, pr)

@@ -42,6 +42,12 @@ class weno_params(ctypes.Structure):
                 ("alpha_thr", ctypes.c_int), ("hybrid", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
+class weno_batch_desc(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("n", ctypes.POINTER(ctypes.c_int)), ("lo", ctypes.POINTER(ctypes.c_double)),
+                ("hi", ctypes.POINTER(ctypes.c_double)), ("t_end", ctypes.POINTER(ctypes.c_double)),
+                ("bc_lo", ctypes.c_int), ("bc_hi", ctypes.c_int), ("max_steps", ctypes.c_int)]
+
+
 _vp = ctypes.c_void_p
 _ip = ctypes.c_int
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -65,6 +71,15 @@ SIGNATURES = {
     "weno_measure_fma_peak": (ctypes.c_int, [_ip, _dp, _dp]),
     "weno_enqueue_steps": (ctypes.c_int, [_vp, ctypes.c_double, _ip]),
     "weno_autotune": (ctypes.c_int, [_vp, _ip, ctypes.POINTER(_ip)]),
+    "weno_batch_create": (ctypes.c_int, [ctypes.POINTER(weno_batch_desc), ctypes.POINTER(weno_params), _vp,
+                                         ctypes.POINTER(_vp)]),
+    "weno_batch_run": (ctypes.c_int, [_vp, _vp]),
+    "weno_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(_ip), ctypes.POINTER(ctypes.c_longlong), _dp]),
+    "weno_batch_autotune": (ctypes.c_int, [_vp, _vp, _ip, ctypes.POINTER(_ip)]),
+    "weno_batch_destroy": (None, [_vp]),
+    "weno_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "weno_batch_solve": (ctypes.c_int, [ctypes.POINTER(weno_batch_desc), ctypes.POINTER(weno_params), _vp, _vp,
+                                        ctypes.POINTER(_ip)]),
     "weno_set_tiles": (ctypes.c_int, [_vp, ctypes.POINTER(_ip)]),
     "weno_conserved_totals_noalloc": (ctypes.c_int, [_ip, ctypes.POINTER(_ip), _dp, _ip, _vp, _vp, _vp]),
     "weno_time_sweeps": (ctypes.c_int, [_vp, _ip, _vp, ctypes.c_size_t, _dp, ctypes.POINTER(ctypes.c_ulonglong)]),
@@ -350,3 +365,118 @@ class Solver:
 
     def time_sweeps(self, reps: int = 5, flush=None):
         return weno_time_sweeps(self.ctx, self.dim, reps, flush)
+
+
+# ----------------------------------------------------------------- batches
+
+def _bcheck(st: int, batch=None):
+    if st != WENO_OK:
+        msg = load().weno_batch_last_error(batch)
+        raise WenoError(st, msg.decode() if msg else "")
+
+
+def _batch_desc(N, lo, hi, t_end, bc_lo=0, bc_hi=0, max_steps=0):
+    N = np.ascontiguousarray(N, dtype=np.int32)
+    lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, dtype=np.float64), N.shape))
+    hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, dtype=np.float64), N.shape))
+    te = np.ascontiguousarray(t_end, dtype=np.float64)
+    d = weno_batch_desc()
+    d.count = int(N.size)
+    d.n = N.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    d.lo = lo.ctypes.data_as(_dp)
+    d.hi = hi.ctypes.data_as(_dp)
+    d.t_end = te.ctypes.data_as(_dp)
+    d.bc_lo, d.bc_hi, d.max_steps = int(bc_lo), int(bc_hi), int(max_steps)
+    return d, (N, lo, hi, te)
+
+
+def weno_batch_create(N, lo, hi, t_end, params: weno_params, bc_lo=0, bc_hi=0, max_steps=0, stream: int = 0) -> int:
+    d, keep = _batch_desc(N, lo, hi, t_end, bc_lo, bc_hi, max_steps)
+    b = _vp()
+    _bcheck(load().weno_batch_create(ctypes.byref(d), ctypes.byref(params), _vp(stream or None), ctypes.byref(b)))
+    return b.value
+
+
+def weno_batch_run(batch: int, U_dev) -> None:
+    _bcheck(load().weno_batch_run(_vp(batch), _vp(_ptr(U_dev))), _vp(batch))
+
+
+def weno_batch_results(batch: int, count: int, raise_on_failure: bool = False):
+    st = np.zeros(count, dtype=np.int32)
+    steps = np.zeros(count, dtype=np.int64)
+    t = np.zeros(count)
+    r = load().weno_batch_results(_vp(batch), st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  steps.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), t.ctypes.data_as(_dp))
+    if r != WENO_OK and (raise_on_failure or r != WENO_ERR_NONPHYSICAL):
+        _bcheck(r, _vp(batch))
+    return st, steps, t
+
+
+def weno_batch_autotune(batch: int, U_dev, trial_steps: int = 4):
+    c = (ctypes.c_int * 2)()
+    _bcheck(load().weno_batch_autotune(_vp(batch), _vp(_ptr(U_dev)), int(trial_steps), c), _vp(batch))
+    return list(c)
+
+
+def weno_batch_destroy(batch: int) -> None:
+    load().weno_batch_destroy(_vp(batch))
+
+
+def weno_batch_solve(N, lo, hi, t_end, params: weno_params, U_dev, bc_lo=0, bc_hi=0, max_steps=0, stream: int = 0):
+    d, keep = _batch_desc(N, lo, hi, t_end, bc_lo, bc_hi, max_steps)
+    st = np.zeros(d.count, dtype=np.int32)
+    r = load().weno_batch_solve(ctypes.byref(d), ctypes.byref(params), _vp(stream or None), _vp(_ptr(U_dev)),
+                                st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if r not in (WENO_OK, WENO_ERR_NONPHYSICAL):
+        _bcheck(r)
+    return st
+
+
+class Batch:
+    """Many independent 1D Euler problems solved by one persistent launch."""
+
+    def __init__(self, N, lo, hi, t_end, precision: str = "fp64", gamma: float = 1.4, bc=(0, 0),
+                 max_steps: int = 0, stream=None, **params):
+        import torch
+        self.N = np.asarray(N, dtype=np.int64)
+        self.count = int(self.N.size)
+        self.offsets = np.concatenate([[0], np.cumsum(3 * self.N)])
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        p = weno_default_params()
+        p.gamma = gamma
+        for k, v in params.items():
+            setattr(p, k, v)
+        p.precision = PRECISIONS[precision]
+        s = stream.cuda_stream if stream is not None else 0
+        self.handle = weno_batch_create(self.N, lo, hi, t_end, p, bc[0], bc[1], max_steps, s)
+
+    def pack(self, states):
+        """Device array holding the states ([3][n_i] each) back to back."""
+        import torch
+        flat = np.concatenate([np.asarray(u, dtype=np.float64).reshape(-1) for u in states])
+        return torch.from_numpy(flat).to("cuda", self.dtype)
+
+    def unpack(self, U_dev):
+        h = U_dev.double().cpu().numpy()
+        return [h[self.offsets[i]:self.offsets[i + 1]].reshape(3, -1) for i in range(self.count)]
+
+    def run(self, U_dev):
+        weno_batch_run(self.handle, U_dev)
+
+    def results(self):
+        return weno_batch_results(self.handle, self.count)
+
+    def autotune(self, U_dev, trial_steps: int = 4):
+        return weno_batch_autotune(self.handle, U_dev, trial_steps)
+
+    def close(self):
+        if self.handle:
+            weno_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
