@@ -83,6 +83,7 @@ def lib():
             L.or_eps_h.argtypes = [cp, ctypes.c_double]
             L.or_fill_ghosts.argtypes = [cp, ctypes.c_double, dp, dp]
             L.or_rhs.argtypes = [cp, ctypes.c_double, dp, dp, ctypes.POINTER(ctypes.c_ubyte), dp]
+            L.or_rhs_jvp.argtypes = [cp, ctypes.c_double, dp, dp, dp, dp]
             L.or_cfl_dt.restype = ctypes.c_double
             L.or_cfl_dt.argtypes = [cp, dp]
             L.or_step.restype = ctypes.c_int
@@ -233,6 +234,19 @@ def rhs(problem: dict, U: np.ndarray, t: float = 0.0, want_flags: bool = False):
         return dU, flags, ratio
     lib().or_rhs(ctypes.byref(c), t, _dp(U), _dp(dU), None, None)
     return dU
+
+
+def rhs_jvp(problem: dict, U: np.ndarray, V: np.ndarray, t: float = 0.0):
+    """(dU/dt, J V): the RHS and its directional derivative along V, with the
+    hybrid flags and LLF maxima held at their values for U (LLF only)."""
+    assert problem.get("splitting", "llf") == "llf"
+    c = make_cfg(problem)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    dU = np.zeros_like(U)
+    JV = np.zeros_like(U)
+    lib().or_rhs_jvp(ctypes.byref(c), t, _dp(U), _dp(V), _dp(dU), _dp(JV))
+    return dU, JV
 
 
 def cfl_dt(problem: dict, U: np.ndarray) -> float:

@@ -106,6 +106,28 @@ static inline Cnt sqrt_r(Cnt a) { g_ops.sqrt_++; return Cnt(std::sqrt(a.v)); }
 static inline Cnt abs_r(Cnt a) { return Cnt(std::fabs(a.v)); }
 static inline double val(Cnt a) { return a.v; }
 
+/* forward-mode dual number (value, derivative) for Jacobian-vector products;
+ * comparisons, max and the hybrid decision act on the value, so flags and
+ * LLF maxima are held fixed along the tangent */
+struct Dual {
+    double v, d;
+    Dual() : v(0), d(0) {}
+    Dual(double x) : v(x), d(0) {}
+    Dual(double x, double dx) : v(x), d(dx) {}
+};
+static inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+static inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+static inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+static inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+static inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+static inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+static inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+static inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
+static inline bool operator<=(Dual a, Dual b) { return a.v <= b.v; }
+static inline Dual sqrt_r(Dual a) { double r = std::sqrt(a.v); return Dual(r, 0.5 * a.d / r); }
+static inline Dual abs_r(Dual a) { return a.v < 0 ? Dual(-a.v, -a.d) : a; }
+static inline double val(Dual a) { return a.v; }
+
 static inline double sqrt_r(double a) { return std::sqrt(a); }
 static inline double abs_r(double a) { return std::fabs(a); }
 static inline double val(double a) { return a; }
@@ -680,6 +702,77 @@ static int rk3_step(Grid& G, double& t, double t_end, double* dt_out)
 }
 
 /* ------------------------------------------------------------------ */
+/* Jacobian-vector product of the semi-discrete operator: the RHS       */
+/* evaluated in dual numbers along the tangent V (ghost cells are       */
+/* linear maps of the interior, fixed inflow states carry no tangent).  */
+/* ------------------------------------------------------------------ */
+static void rhs_jvp_grid(const or_cfg& c, double t, const double* Ui, const double* Vi, double* dU, double* JV)
+{
+    Grid G(c), H(c);
+    G.load_interior(Ui);
+    H.load_interior(Vi);
+    for (int a = 0; a < G.dim_eff; ++a) {
+        fill_ghosts_dir(G, a, t);
+        fill_ghosts_dir(H, a, t);
+    }
+    /* fixed inflow ghosts: zero tangent (the state arrays are otherwise linear) */
+    for (int a = 0; a < G.dim_eff; ++a)
+        for (int side = 0; side < 2; ++side) {
+            const int bc = side == 0 ? c.bc_lo[a] : c.bc_hi[a];
+            if (bc != BC_INFLOW && bc != BC_DMR_BOTTOM && bc != BC_DMR_TOP) continue;
+            int lim[3] = {G.n[0], G.n[1], G.n[2]};
+            lim[a] = 1;
+            for (int p2 = 0; p2 < lim[2]; ++p2)
+                for (int p1 = 0; p1 < lim[1]; ++p1)
+                    for (int p0 = 0; p0 < lim[0]; ++p0)
+                        for (int gl = 1; gl <= NG; ++gl) {
+                            int ix[3] = {p0, p1, p2};
+                            ix[a] = side == 0 ? -gl : G.n[a] - 1 + gl;
+                            bool fixed = bc == BC_INFLOW || bc == BC_DMR_TOP;
+                            if (bc == BC_DMR_BOTTOM) fixed = G.center(0, ix[0]) < 1.0 / 6.0;
+                            if (fixed)
+                                for (int v = 0; v < G.nv; ++v) H.at(v, ix[0], ix[1], ix[2]) = 0.0;
+                        }
+        }
+    const int nv = G.nv;
+    const size_t ni = G.interior_size();
+    for (size_t p = 0; p < nv * ni; ++p) { dU[p] = 0.0; JV[p] = 0.0; }
+    for (int a = 0; a < G.dim_eff; ++a) {
+        const int na = G.n[a];
+        const double eps_h = eps_h_of(c, G.dx[a]);
+        int lim[3] = {G.n[0], G.n[1], G.n[2]};
+        lim[a] = 1;
+        std::vector<CellQ<Dual>> line(na + 2 * NG);
+        std::vector<Dual> Fh((size_t)(na + 1) * nv);
+        double zeros[5] = {0, 0, 0, 0, 0};
+        for (int p2 = 0; p2 < lim[2]; ++p2)
+            for (int p1 = 0; p1 < lim[1]; ++p1)
+                for (int p0 = 0; p0 < lim[0]; ++p0) {
+                    for (int m = -NG; m < na + NG; ++m) {
+                        int ix[3] = {p0, p1, p2};
+                        ix[a] = m;
+                        Dual Uc[5];
+                        for (int v = 0; v < nv; ++v)
+                            Uc[v] = Dual(G.at(v, ix[0], ix[1], ix[2]), H.at(v, ix[0], ix[1], ix[2]));
+                        cell_quantities(c, a, Uc, line[m + NG]);
+                    }
+                    for (int i = 0; i <= na; ++i)
+                        face_flux(c, a, eps_h, &line[i - 3 + NG], zeros, &Fh[(size_t)i * nv], (FaceInfo*)nullptr);
+                    for (int i = 0; i < na; ++i) {
+                        int ix[3] = {p0, p1, p2};
+                        ix[a] = i;
+                        size_t cell = ((size_t)ix[2] * G.n[1] + ix[1]) * G.n[0] + ix[0];
+                        for (int v = 0; v < nv; ++v) {
+                            Dual r = (Fh[(size_t)(i + 1) * nv + v] - Fh[(size_t)i * nv + v]) / Dual(G.dx[a]);
+                            dU[(size_t)v * ni + cell] -= r.v;
+                            JV[(size_t)v * ni + cell] -= r.d;
+                        }
+                    }
+                }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* exact Riemann solver of the 1D Euler equations (Godunov's problem)  */
 /* Star pressure from f_L(p) + f_R(p) + u_R - u_L = 0 by Newton's      */
 /* method, shock relations (Rankine-Hugoniot) and rarefaction relations*/
@@ -862,6 +955,12 @@ void or_rhs(const or_cfg* c, double t, const double* U, double* dU,
     std::vector<double> L;
     rhs_grid(G, t, L, flags, ratio);
     std::memcpy(dU, L.data(), L.size() * sizeof(double));
+}
+
+/* RHS and its Jacobian-vector product J(U) V at time t (LLF splitting) */
+void or_rhs_jvp(const or_cfg* c, double t, const double* U, const double* V, double* dU, double* JV)
+{
+    rhs_jvp_grid(*c, t, U, V, dU, JV);
 }
 
 /* CFL time step of state U (no clipping) */

@@ -503,3 +503,35 @@ def test_nonphysical_state_reported_and_restored():
     st, t, dt = orc.step(prob, U, 0.0, 1.0)
     assert st == 3
     assert np.array_equal(U, U0)
+
+
+# ---------------------------------------------------------------------------
+# Jacobian-vector product of the semi-discrete operator (adjoint checks)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,n", [(1, [64]), (2, [24, 16]), (3, [10, 8, 7])])
+def test_rhs_jvp_matches_central_differences(dim, n):
+    """Dual-number J V against FP64 central differences on smooth data (no
+    flag or LLF-argmax changes under the perturbation)."""
+    prob, U = P.random_state(dim, n, seed=5, kind="smooth")
+    rng = np.random.default_rng(0)
+    V = rng.normal(size=U.shape) * np.abs(U).mean(axis=tuple(range(1, dim + 1)), keepdims=True)
+    r0, jv = orc.rhs_jvp(prob, U, V)
+    assert np.array_equal(r0, orc.rhs(prob, U))
+    h = 1e-7
+    _, f0, _ = orc.rhs(prob, U, 0.0, want_flags=True)
+    _, fp, _ = orc.rhs(prob, U + h * V, 0.0, want_flags=True)
+    _, fm, _ = orc.rhs(prob, U - h * V, 0.0, want_flags=True)
+    assert np.array_equal(fp, f0) and np.array_equal(fm, f0)
+    fd = (orc.rhs(prob, U + h * V) - orc.rhs(prob, U - h * V)) / (2 * h)
+    assert np.max(np.abs(fd - jv)) <= 1e-6 * np.max(np.abs(jv))
+
+
+def test_rhs_jvp_is_linear_in_the_tangent():
+    prob, U = P.random_state(2, [20, 12], seed=9, kind="mixed")
+    rng = np.random.default_rng(1)
+    V1, V2 = rng.normal(size=U.shape), rng.normal(size=U.shape)
+    _, a = orc.rhs_jvp(prob, U, V1)
+    _, b = orc.rhs_jvp(prob, U, V2)
+    _, c = orc.rhs_jvp(prob, U, 2.0 * V1 - 3.0 * V2)
+    assert np.allclose(c, 2.0 * a - 3.0 * b, rtol=1e-9, atol=1e-9 * np.max(np.abs(c)))
