@@ -125,6 +125,21 @@ weno_status weno_get_state(weno_ctx* ctx, void* U, int on_device, double* t);
  * stream; returns WENO_ERR_CUDA if a launch fails. */
 weno_status weno_rhs(weno_ctx* ctx, const void* U_dev, void* dUdt_dev, double t);
 
+/* Vector-Jacobian product of the semi-discrete operator (the adjoint of
+ * weno_rhs; the paper does not differentiate its scheme):
+ *     gU = (d RHS / d U)^T w   at U = U_dev, ghost cells filled at time t.
+ * The hybrid flag of each face (Eq. eqhy) and the stencil cell attaining
+ * each LLF maximum (Eq. flxuspliting) are held at their values for U_dev
+ * (first index on ties): the result is the derivative of the active smooth
+ * piece.  The backward pass recomputes every forward quantity (Roe state,
+ * detector, projections, nonlinear weights); nothing is stored between
+ * calls.  Ghost-cell contributions are mapped back through the boundary
+ * conditions (fixed inflow states receive none).  U_dev, w_dev, gU_dev:
+ * interior-only device arrays of the state's shape and element type.
+ * Deterministic (no atomics).  Asynchronous; WENO_ERR_CUDA if a launch or
+ * an allocation of the backward buffers fails. */
+weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, void* gU_dev, double t);
+
 /* Per-face hybrid flags of U_dev at time t: 1 where the linear upwind scheme
  * is used (Eq. eqhy, sigma_{j+1/2} = 1), 0 where the regularized WENO-IS flux
  * is used.  flags_dev: uint8 device array holding, for each direction d in

@@ -1,0 +1,599 @@
+// Hand-written adjoint (vector-Jacobian product) of the semi-discrete
+// operator dU/dt = -sum_d (F_{j+1/2} - F_{j-1/2}) / dx_d.
+//
+// For a cotangent w (one value per cell and variable) the face flux F_f of
+// direction d receives the cotangent phi_f = (w_{j+1} - w_j) / dx_d (w = 0
+// outside the domain), and gU = sum_f (dF_f / dU_stencil)^T phi_f.  Every
+// face recomputes its forward quantities (Roe state, detector, LLF speeds,
+// projections, reconstructions: nothing is stored by the forward pass) and
+// then runs the reverse of each step:
+//   back-projection (Eq. reconstruction2)  -> back_proj_adj
+//   reconstruction (Eq. eq6, eq11, eq18, eq8-r) -> recon_adj
+//   splitting and projection (Eq. flxuspliting, eqchara) -> proj_all_adj
+//   regularization parameter (Eq. eq27-29) and detector (Eq. eq28)
+//   Roe average (Sec. 2.4 step (1)) -> roe_adj
+//   cell primitives and physical flux -> cell_adj
+// The hybrid flag and the cell that attains each LLF maximum are held at
+// their forward values (first index on ties): the operator is piecewise
+// smooth and this is the derivative of the active piece.
+//
+// Accumulation is deterministic: a tile of SEG cells recomputes the SEG + 5
+// faces that touch its cells, writes each face's contribution to the six
+// stencil-cell records in shared memory, and gathers them per cell.
+// Contributions to ghost cells go to a per-line buffer that a second kernel
+// maps back through the boundary conditions.
+#pragma once
+
+#include "weno_kernels.cuh"
+
+namespace wis {
+
+template <typename T> __device__ __forceinline__ T sgn(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
+
+// record bars of one cell (NQ entries, same layout as CellLayout) -> dU
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void cell_adj(const T* U, T gamma, const T* qb, T* Ub)
+{
+    using CL = CellLayout<DIM>;
+    constexpr int NV = DIM + 2;
+    const T gm1 = gamma - T(1);
+    const T rho = U[0];
+    const T isq = Ar<T>::rsqrt_(rho);
+    const T irho = isq * isq;
+    T m2 = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) m2 = fmaT(U[1 + k], U[1 + k], m2);
+    const T E = U[DIM + 1];
+    const T p = gm1 * fmaT(T(-0.5) * irho, m2, E);
+    const T c = Ar<T>::sqrt_(gamma * p * irho);
+    const T un = U[1 + DIR] * irho;
+    const T Ep = E + p;
+
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Ub[v] = qb[CL::U + v];
+    T unb = T(0), cb = T(0), isqb = T(0), Epb = T(0), pb = T(0), irhob = T(0), m2b = T(0);
+    const T s1 = sgn(un - c), s0 = sgn(un), s2 = sgn(un + c);
+    unb += qb[CL::LM] * s1; cb -= qb[CL::LM] * s1;
+    unb += qb[CL::L0] * s0;
+    unb += qb[CL::LP] * s2; cb += qb[CL::LP] * s2;
+    Ub[0] += qb[CL::SQ] * isq; isqb += qb[CL::SQ] * rho;
+    Epb += qb[CL::SH] * isq; isqb += qb[CL::SH] * Ep;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { Ub[1 + k] += qb[CL::SU + k] * isq; isqb += qb[CL::SU + k] * U[1 + k]; }
+    Epb += qb[CL::F + DIM + 1] * un; unb += qb[CL::F + DIM + 1] * Ep;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { Ub[1 + k] += qb[CL::F + 1 + k] * un; unb += qb[CL::F + 1 + k] * U[1 + k]; }
+    pb += qb[CL::F + 1 + DIR];
+    Ub[1 + DIR] += qb[CL::F + 0];
+    Ub[DIM + 1] += Epb; pb += Epb;
+    Ub[1 + DIR] += unb * irho; irhob += unb * U[1 + DIR];
+    // c = sqrt(gamma p irho)
+    const T cc = cb / (T(2) * c);
+    pb += cc * gamma * irho; irhob += cc * gamma * p;
+    // p = gm1 (E - irho m2 / 2)
+    Ub[DIM + 1] += pb * gm1; irhob -= pb * gm1 * T(0.5) * m2; m2b -= pb * gm1 * T(0.5) * irho;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) Ub[1 + k] += T(2) * U[1 + k] * m2b;
+    isqb += T(2) * isq * irhob;
+    Ub[0] += isqb * (T(-0.5) * isq * irho);
+}
+
+template <typename T, int DIM> struct RoeBar {
+    T u[DIM];
+    T c, ic, H, b1, hq2, rt;
+};
+
+template <typename T, int DIM>
+__device__ __forceinline__ void zero(RoeBar<T, DIM>& b)
+{
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) b.u[k] = T(0);
+    b.c = b.ic = b.H = b.b1 = b.hq2 = b.rt = T(0);
+}
+
+// adjoint of w = L x (proj_all): accumulates xb and rb
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void proj_all_adj(const Roe<T, DIM>& r, const T* x, const T* wb, T* xb,
+                                             RoeBar<T, DIM>& rb)
+{
+    constexpr int LAST = DIM + 1;
+    T dot = r.u[0] * x[1];
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) dot = fmaT(r.u[k], x[1 + k], dot);
+    const T y = fmaT(r.hq2, x[0], x[DIM + 1]) - dot;
+    const T z = fmaT(r.u[DIR], x[0], -x[1 + DIR]);
+    const T t1b = T(0.5) * wb[0] - wb[1] + T(0.5) * wb[LAST];
+    const T ab = T(0.5) * (wb[0] - wb[LAST]);
+    int s = 2;
+#pragma unroll
+    for (int t = 0; t < DIM; ++t) {
+        if (t == DIR) continue;
+        xb[1 + t] += wb[s];
+        xb[0] -= wb[s] * r.u[t];
+        rb.u[t] -= wb[s] * x[0];
+        ++s;
+    }
+    xb[0] += wb[1];
+    const T zb = ab * r.ic;
+    rb.ic += ab * z;
+    rb.u[DIR] += zb * x[0];
+    xb[0] += zb * r.u[DIR];
+    xb[1 + DIR] -= zb;
+    rb.b1 += t1b * y;
+    const T yb = t1b * r.b1;
+    rb.hq2 += yb * x[0];
+    xb[0] += yb * r.hq2;
+    xb[DIM + 1] += yb;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { rb.u[k] -= yb * x[1 + k]; xb[1 + k] -= yb * r.u[k]; }
+}
+
+// adjoint of out = R w (back_proj_add): sets wb, accumulates rb
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void back_proj_adj(const Roe<T, DIM>& r, const T* w, const T* ob, T* wb,
+                                              RoeBar<T, DIM>& rb)
+{
+    constexpr int LAST = DIM + 1;
+    const T sum = w[0] + w[1] + w[LAST];
+    const T dif = w[LAST] - w[0];
+    const T oE = ob[LAST];
+    T sumb = ob[0];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { sumb = fmaT(ob[1 + k], r.u[k], sumb); rb.u[k] += ob[1 + k] * sum; }
+    const T difb = (ob[1 + DIR] + oE * r.u[DIR]) * r.c;
+    rb.c += (ob[1 + DIR] + oE * r.u[DIR]) * dif;
+    rb.u[DIR] += oE * r.c * dif;
+#pragma unroll
+    for (int s = 0; s <= LAST; ++s) wb[s] = T(0);
+    int s = 2;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        if (k == DIR) continue;
+        wb[s] = ob[1 + k] + oE * r.u[k];
+        rb.u[k] += oE * w[s];
+        ++s;
+    }
+    rb.H += oE * (w[0] + w[LAST]);
+    rb.hq2 += oE * w[1];
+    wb[0] += oE * r.H + sumb - difb;
+    wb[1] += oE * r.hq2 + sumb;
+    wb[LAST] += oE * r.H + sumb + difb;
+}
+
+// adjoint of the Roe average; gab/gbb: record bars of cells j and j+1
+template <typename T, int DIM, typename GA, typename GB>
+__device__ __forceinline__ void roe_adj(GA get_a, GB get_b, T gamma, const Roe<T, DIM>& r, RoeBar<T, DIM> rb,
+                                        T* gab, T* gbb)
+{
+    using CL = CellLayout<DIM>;
+    const T gm1 = gamma - T(1);
+    const T sa = get_a(CL::SQ), sb = get_b(CL::SQ);
+    const T inv = Ar<T>::rcp(sa + sb);
+    // b1 = gm1 ic^2; c = c2 ic (= sqrt c2); ic = c2^-1/2; c2 = gm1 (H - hq2)
+    rb.ic += rb.b1 * gm1 * T(2) * r.ic;
+    const T ic3 = r.ic * r.ic * r.ic;
+    const T c2b = rb.c * T(0.5) * r.ic - T(0.5) * rb.ic * ic3;
+    rb.H += c2b * gm1;
+    rb.hq2 -= c2b * gm1;
+    T invb = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const T ub = rb.u[k] + r.u[k] * rb.hq2;
+        gab[CL::SU + k] += ub * inv;
+        gbb[CL::SU + k] += ub * inv;
+        invb += ub * (get_a(CL::SU + k) + get_b(CL::SU + k));
+    }
+    gab[CL::SH] += rb.H * inv;
+    gbb[CL::SH] += rb.H * inv;
+    invb += rb.H * (get_a(CL::SH) + get_b(CL::SH));
+    const T sb_ = -invb * inv * inv;
+    gab[CL::SQ] += sb_ + rb.rt * sb;
+    gbb[CL::SQ] += sb_ + rb.rt * sa;
+}
+
+// adjoint of the reconstruction: fb -> bars of a..e (accumulated) and of lam
+template <typename T>
+__device__ __forceinline__ void recon_adj(T a, T b, T c, T d, T e, T lam, T eps, T fb, T* xb, T& lamb)
+{
+    const T q0 = T(0.5) * (c + d);
+    const T q1 = fmaT(T(1.5), c, T(-0.5) * b);
+    const T q2 = fmaT(T(1.0 / 3.0), c, fmaT(T(5.0 / 6.0), d, T(-1.0 / 6.0) * e));
+    const T q3 = fmaT(T(1.0 / 3.0), a, fmaT(T(-7.0 / 6.0), b, T(11.0 / 6.0) * c));
+    const T b0 = (d - c) * (d - c), b1 = (c - b) * (c - b);
+    const T t2 = fmaT(T(-2), d, c) + e, s2 = fmaT(T(-4), d, T(3) * c) + e;
+    const T be2 = fmaT(T(13.0 / 12.0), t2 * t2, T(0.25) * (s2 * s2));
+    const T t3 = fmaT(T(-2), b, a) + c, s3 = fmaT(T(-4), b, a) + T(3) * c;
+    const T be3 = fmaT(T(13.0 / 12.0), t3 * t3, T(0.25) * (s3 * s3));
+    const T tt = fmaT(T(-4), b + d, a + e) + T(6) * c, st = fmaT(T(2), b - d, e - a);
+    const T tau = fmaT(T(13.0 / 12.0), tt * tt, T(0.25) * (st * st));
+    const T te = fmaT(T(-2), c, b + d);
+    const T E = (te * te) * T(1.0 / 45.0);
+    const T dk[4] = {T(0.4), T(0.2), T(0.3), T(0.1)};
+    const T beta[4] = {b0, b1, be2, be3};
+    const T lt = lam * tau;
+    T D[4], al[4];
+    T S = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        D[k] = fmaT(lam, beta[k], (k < 2 ? E : T(0)) + eps);
+        al[k] = dk[k] * (T(1) + lt / D[k]);
+        S += al[k];
+    }
+    const T iS = T(1) / S;
+    const T q[4] = {q0, q1, q2, q3};
+    T fh = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fh = fmaT(al[k] * iS, q[k], fh);
+    // reverse
+    T qb[4], ltb = T(0), betab[4], Eb = T(0);
+    lamb = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        qb[k] = fb * al[k] * iS;
+        const T alb = (q[k] - fh) * fb * iS;
+        const T r = alb * dk[k] / D[k];
+        ltb += r;
+        const T Db = -r * (lt / D[k]);
+        lamb += Db * beta[k];
+        betab[k] = Db * lam;
+        if (k < 2) Eb += Db;
+    }
+    lamb += ltb * tau;
+    const T taub = ltb * lam;
+    T ab = T(0), bb = T(0), cb = T(0), db = T(0), eb = T(0);
+    // beta_0, beta_1
+    db += T(2) * (d - c) * betab[0]; cb -= T(2) * (d - c) * betab[0];
+    cb += T(2) * (c - b) * betab[1]; bb -= T(2) * (c - b) * betab[1];
+    // beta_2
+    T tb = betab[2] * T(13.0 / 6.0) * t2, sb = betab[2] * T(0.5) * s2;
+    cb += tb + T(3) * sb; db += T(-2) * tb - T(4) * sb; eb += tb + sb;
+    // beta_3
+    tb = betab[3] * T(13.0 / 6.0) * t3; sb = betab[3] * T(0.5) * s3;
+    ab += tb + sb; bb += T(-2) * tb - T(4) * sb; cb += tb + T(3) * sb;
+    // tau_5
+    tb = taub * T(13.0 / 6.0) * tt; sb = taub * T(0.5) * st;
+    ab += tb - sb; eb += tb + sb; bb += T(-4) * tb + T(2) * sb; db += T(-4) * tb - T(2) * sb; cb += T(6) * tb;
+    // E
+    tb = Eb * T(2.0 / 45.0) * te;
+    bb += tb; cb -= T(2) * tb; db += tb;
+    // candidate fluxes
+    ab += qb[3] * T(1.0 / 3.0);
+    bb += T(-0.5) * qb[1] + T(-7.0 / 6.0) * qb[3];
+    cb += T(0.5) * qb[0] + T(1.5) * qb[1] + T(1.0 / 3.0) * qb[2] + T(11.0 / 6.0) * qb[3];
+    db += T(0.5) * qb[0] + T(5.0 / 6.0) * qb[2];
+    eb += T(-1.0 / 6.0) * qb[2];
+    xb[0] += ab; xb[1] += bb; xb[2] += cb; xb[3] += db; xb[4] += eb;
+}
+
+struct VjpArgs {
+    const void* U;      // ghosted state, ghosts filled
+    const void* W;      // ghosted cotangent, ghosts zero
+    void* G;            // ghosted gradient accumulator (interior written)
+    void* ghost;        // [line][6][NV] gradients of ghost cells
+    int accumulate;     // 0: G = ..., 1: G += ...
+    int n[3];
+    long long sy, sz, sv, off0;
+    double inv_dx, eps_h, gamma, eps, c_lambda;
+    int hybrid;
+};
+
+template <int DIM> struct VjpTile { static constexpr int SEG = 59, NT = 64; };
+
+template <typename T, int DIM>
+struct VjpSmem {
+    static constexpr int SEG = VjpTile<DIM>::SEG;
+    static constexpr int NF = SEG + 5;          // faces c0-2 .. c0+SEG+2
+    static constexpr int NC = SEG + 10;         // cells c0-5 .. c0+SEG+4
+    static constexpr int NQ = CellLayout<DIM>::NQ;
+    static constexpr int NV = DIM + 2;
+    static constexpr size_t bytes = sizeof(T) * ((size_t)NQ * NC + (size_t)NV * NC + (size_t)NF * 6 * NQ);
+};
+
+// one direction of the VJP: tile = one grid line segment of SEG cells
+template <typename T, int DIM, int DIR>
+__global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
+{
+    using CL = CellLayout<DIM>;
+    using SM = VjpSmem<T, DIM>;
+    constexpr int NV = DIM + 2, NQ = CL::NQ, SEG = SM::SEG, NF = SM::NF, NC = SM::NC;
+    constexpr int NT = VjpTile<DIM>::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ][NC]
+    T* wq = cq + NQ * NC;                     // [NV][NC] cotangent
+    T* G = wq + NV * NC;                      // [NF][6][NQ] record bars per face
+
+    const int nd = a.n[DIR];
+    const int c0 = blockIdx.x * SEG;
+    // line coordinates: the two indices other than DIR
+    int i = 0, j = 0, k = 0;
+    if (DIR == 0) { j = blockIdx.y; k = blockIdx.z; }
+    else if (DIR == 1) { i = blockIdx.y; k = blockIdx.z; }
+    else { i = blockIdx.y; j = blockIdx.z; }
+    const long long sd = DIR == 0 ? 1LL : (DIR == 1 ? a.sy : a.sz);
+    const long long base = a.off0 + (long long)i + (long long)j * a.sy + (long long)k * a.sz;
+    const T* Ug = reinterpret_cast<const T*>(a.U);
+    const T* Wg = reinterpret_cast<const T*>(a.W);
+    const T gamma = T(a.gamma);
+
+    // stage cells c0-5 .. c0+SEG+4 that exist (-3 .. nd+2)
+    for (int p = threadIdx.x; p < NC; p += NT) {
+        const int cell = c0 - 5 + p;
+        if (cell >= -3 && cell <= nd + 2) {
+            const long long g = base + (long long)cell * sd;
+            T U[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) { U[v] = Ug[g + v * a.sv]; wq[v * NC + p] = Wg[g + v * a.sv]; }
+            T q[NQ];
+            cell_prepare<T, DIM, DIR>(U, gamma, q);
+#pragma unroll
+            for (int kk = 0; kk < NQ; ++kk) cq[kk * NC + p] = q[kk];
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) wq[v * NC + p] = T(0);
+        }
+    }
+    for (int idx = threadIdx.x; idx < NF * 6 * NQ; idx += NT) G[idx] = T(0);
+    __syncthreads();
+
+    // ---- per face: forward recompute and reverse -------------------------
+    const T lim0 = T(3600.0 * a.eps_h);
+    const T lam_k = T(a.c_lambda / 3600.0);
+    const T eps = T(a.eps), inv_dx = T(a.inv_dx);
+    for (int f = threadIdx.x; f < NF; f += NT) {
+        const int face = c0 - 2 + f;            // face i' between cells i'-1 and i'
+        if (face < 0 || face > nd) continue;
+        const int p0 = f;                       // tile index of stencil cell j-2 = face-3
+        auto rec = [&](int m, int kk) -> T { return cq[kk * NC + p0 + m]; };
+        T* Gf = G + (size_t)f * 6 * NQ;         // bars of the six stencil cells
+        // cotangent of the face flux: (w_{right} - w_{left}) / dx
+        T phi[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) phi[v] = (wq[v * NC + p0 + 3] - wq[v * NC + p0 + 2]) * inv_dx;
+
+        auto ga = [&](int kk) -> T { return rec(2, kk); };
+        auto gb = [&](int kk) -> T { return rec(3, kk); };
+        const Roe<T, DIM> r = roe_state<T, DIM>(ga, gb, gamma);
+        RoeBar<T, DIM> rb;
+        zero(rb);
+        T dU[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const int kk = CL::U + v;
+            dU[v] = fmaT(T(10), rec(2, kk) - rec(3, kk), fmaT(T(5), rec(4, kk) - rec(1, kk), rec(0, kk) - rec(5, kk)));
+        }
+        T w[NV];
+        proj_all<T, DIM, DIR>(r, dU, w);
+        const T lim = lim0 * (r.rt * r.rt);
+        bool smooth = a.hybrid != 0;
+#pragma unroll
+        for (int s = 0; s < NV; ++s) smooth = smooth && lt_nn(w[s] * w[s], lim);
+        // LLF speeds and the cells attaining them
+        T am = rec(0, CL::LM), a0 = rec(0, CL::L0), ap = rec(0, CL::LP);
+        int im = 0, i0 = 0, ip = 0;
+#pragma unroll
+        for (int m = 1; m < 6; ++m) {
+            if (rec(m, CL::LM) > am) { am = rec(m, CL::LM); im = m; }
+            if (rec(m, CL::L0) > a0) { a0 = rec(m, CL::L0); i0 = m; }
+            if (rec(m, CL::LP) > ap) { ap = rec(m, CL::LP); ip = m; }
+        }
+        T alb_m = T(0), alb_0 = T(0), alb_p = T(0);
+        T wb[NV];
+#pragma unroll
+        for (int s = 0; s < NV; ++s) wb[s] = T(0);
+        if (smooth) {
+            // F = [central(F) + R (alpha o w)] / 60
+            T Fb[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Fb[v] = phi[v] * T(1.0 / 60.0);
+            const T cf[6] = {T(1), T(-8), T(37), T(37), T(-8), T(1)};
+#pragma unroll
+            for (int m = 0; m < 6; ++m)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Gf[m * NQ + CL::F + v] += cf[m] * Fb[v];
+            T aw[NV], awb[NV];
+            aw[0] = am * w[0];
+#pragma unroll
+            for (int s = 1; s < NV - 1; ++s) aw[s] = a0 * w[s];
+            aw[NV - 1] = ap * w[NV - 1];
+            back_proj_adj<T, DIM, DIR>(r, aw, Fb, awb, rb);
+            alb_m += awb[0] * w[0];
+            wb[0] += awb[0] * am;
+#pragma unroll
+            for (int s = 1; s < NV - 1; ++s) { alb_0 += awb[s] * w[s]; wb[s] += awb[s] * a0; }
+            alb_p += awb[NV - 1] * w[NV - 1];
+            wb[NV - 1] += awb[NV - 1] * ap;
+        } else {
+            // projections of the six cells, all fields
+            T vv[6][NV], gg[6][NV];
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                T xu[NV], xf[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) { xu[v] = rec(m, CL::U + v); xf[v] = rec(m, CL::F + v); }
+                proj_all<T, DIM, DIR>(r, xu, vv[m]);
+                proj_all<T, DIM, DIR>(r, xf, gg[m]);
+            }
+            const T irt2 = T(1) / (r.rt * r.rt);
+            T wch[NV];
+            T lam[NV];
+#pragma unroll
+            for (int s = 0; s < NV; ++s) {
+                const T al = s == 0 ? am : (s == NV - 1 ? ap : a0);
+                lam[s] = lam_k * (w[s] * w[s]) * irt2;
+                T fp[6], fm[6];
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    const T h = T(0.5) * gg[m][s], kq = T(0.5) * al * vv[m][s];
+                    fp[m] = h + kq;
+                    fm[m] = h - kq;
+                }
+                wch[s] = recon<T>(fp[0], fp[1], fp[2], fp[3], fp[4], lam[s], eps) +
+                         recon<T>(fm[5], fm[4], fm[3], fm[2], fm[1], lam[s], eps);
+            }
+            T wchb[NV];
+            back_proj_adj<T, DIM, DIR>(r, wch, phi, wchb, rb);
+            T vb[6][NV], gbar[6][NV];
+#pragma unroll
+            for (int m = 0; m < 6; ++m)
+#pragma unroll
+                for (int s = 0; s < NV; ++s) { vb[m][s] = T(0); gbar[m][s] = T(0); }
+#pragma unroll
+            for (int s = 0; s < NV; ++s) {
+                const T al = s == 0 ? am : (s == NV - 1 ? ap : a0);
+                T fp[6], fm[6];
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    const T h = T(0.5) * gg[m][s], kq = T(0.5) * al * vv[m][s];
+                    fp[m] = h + kq;
+                    fm[m] = h - kq;
+                }
+                T xp[5] = {T(0), T(0), T(0), T(0), T(0)}, xm[5] = {T(0), T(0), T(0), T(0), T(0)};
+                T lbp, lbm;
+                recon_adj<T>(fp[0], fp[1], fp[2], fp[3], fp[4], lam[s], eps, wchb[s], xp, lbp);
+                recon_adj<T>(fm[5], fm[4], fm[3], fm[2], fm[1], lam[s], eps, wchb[s], xm, lbm);
+                // fm input order was m = 5, 4, 3, 2, 1
+                T fpb[6] = {xp[0], xp[1], xp[2], xp[3], xp[4], T(0)};
+                T fmb[6] = {T(0), xm[4], xm[3], xm[2], xm[1], xm[0]};
+                T alb = T(0);
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    gbar[m][s] += T(0.5) * (fpb[m] + fmb[m]);
+                    vb[m][s] += T(0.5) * al * (fpb[m] - fmb[m]);
+                    alb += T(0.5) * vv[m][s] * (fpb[m] - fmb[m]);
+                }
+                if (s == 0) alb_m += alb;
+                else if (s == NV - 1) alb_p += alb;
+                else alb_0 += alb;
+                // lam = c w^2 / (3600 rt^2)
+                const T lb = lbp + lbm;
+                wb[s] += lb * T(2) * lam_k * w[s] * irt2;
+                rb.rt += lb * (T(-2) * lam[s] / r.rt);
+            }
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                T xu[NV], xf[NV], xub[NV], xfb[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    xu[v] = rec(m, CL::U + v); xf[v] = rec(m, CL::F + v);
+                    xub[v] = T(0); xfb[v] = T(0);
+                }
+                proj_all_adj<T, DIM, DIR>(r, xu, vb[m], xub, rb);
+                proj_all_adj<T, DIM, DIR>(r, xf, gbar[m], xfb, rb);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    Gf[m * NQ + CL::U + v] += xub[v];
+                    Gf[m * NQ + CL::F + v] += xfb[v];
+                }
+            }
+        }
+        // detector: w = L dU, dU = (U0 - U5) + 5 (U4 - U1) + 10 (U2 - U3)
+        T dUb[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dUb[v] = T(0);
+        proj_all_adj<T, DIM, DIR>(r, dU, wb, dUb, rb);
+        const T cd[6] = {T(1), T(-5), T(10), T(-10), T(5), T(-1)};
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Gf[m * NQ + CL::U + v] += cd[m] * dUb[v];
+        Gf[im * NQ + CL::LM] += alb_m;
+        Gf[i0 * NQ + CL::L0] += alb_0;
+        Gf[ip * NQ + CL::LP] += alb_p;
+        roe_adj<T, DIM>(ga, gb, gamma, r, rb, Gf + 2 * NQ, Gf + 3 * NQ);
+    }
+    __syncthreads();
+
+    // ---- gather per cell: faces i' in [i-2, i+3], stencil slot m = i - i' + 3
+    T* Gg = reinterpret_cast<T*>(a.G);
+    T* ghost = reinterpret_cast<T*>(a.ghost);
+    const bool first = c0 == 0, last = c0 + SEG >= nd;
+    for (int p = threadIdx.x; p < SEG + 6; p += NT) {
+        const int cell = c0 - 3 + p;   // owned cells c0..c0+SEG-1 and boundary ghosts
+        const bool owned = cell >= c0 && cell < c0 + SEG && cell < nd;
+        const bool gl = first && cell < 0 && cell >= -3;
+        const bool gr = last && cell >= nd && cell <= nd + 2;
+        if (!owned && !gl && !gr) continue;
+        T qb[NQ];
+#pragma unroll
+        for (int kk = 0; kk < NQ; ++kk) qb[kk] = T(0);
+        for (int fi = cell - 2; fi <= cell + 3; ++fi) {
+            if (fi < 0 || fi > nd) continue;
+            const int f = fi - (c0 - 2);
+            if (f < 0 || f >= NF) continue;
+            const int m = cell - fi + 3;
+            const T* src = G + ((size_t)f * 6 + m) * NQ;
+#pragma unroll
+            for (int kk = 0; kk < NQ; ++kk) qb[kk] += src[kk];
+        }
+        const int pc = cell - (c0 - 5);
+        T U[NV], Ub[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = cq[(CL::U + v) * NC + pc];
+        cell_adj<T, DIM, DIR>(U, gamma, qb, Ub);
+        if (owned) {
+            const long long g = base + (long long)cell * sd;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                if (a.accumulate) Gg[g + v * a.sv] += Ub[v];
+                else Gg[g + v * a.sv] = Ub[v];
+            }
+        } else {
+            const long long line = DIR == 0 ? ((long long)k * a.n[1] + j)
+                                            : (DIR == 1 ? ((long long)k * a.n[0] + i) : ((long long)j * a.n[0] + i));
+            const int slot = gl ? (-cell - 1) : (3 + cell - nd);   // 0..2 left (-1,-2,-3), 3..5 right
+#pragma unroll
+            for (int v = 0; v < NV; ++v) ghost[(line * 6 + slot) * NV + v] = Ub[v];
+        }
+    }
+}
+
+// ghost-cell gradients back to the interior cells they copy (the adjoint of
+// the boundary conditions); fixed inflow states receive nothing
+template <typename T, int DIM>
+__global__ void k_ghost_adj(GhostArgs a, const void* ghost_, void* G_)
+{
+    constexpr int NV = DIM + 2;
+    const int d = a.dir;
+    const int nd = a.n[d];
+    int e0, e1;
+    if (d == 0) { e0 = a.n[1]; e1 = a.n[2]; }
+    else if (d == 1) { e0 = a.n[0]; e1 = a.n[2]; }
+    else { e0 = a.n[0]; e1 = a.n[1]; }
+    const long long lines = (long long)e0 * e1;
+    const long long sd = d == 0 ? 1LL : (d == 1 ? a.sy : a.sz);
+    const T* ghost = reinterpret_cast<const T*>(ghost_);
+    T* G = reinterpret_cast<T*>(G_);
+    for (long long ln = blockIdx.x * (long long)blockDim.x + threadIdx.x; ln < lines;
+         ln += (long long)gridDim.x * blockDim.x) {
+        const int p0 = (int)(ln % e0), p1 = (int)(ln / e0);
+        int i, j, k;
+        if (d == 0) { i = 0; j = p0; k = p1; }
+        else if (d == 1) { i = p0; j = 0; k = p1; }
+        else { i = p0; j = p1; k = 0; }
+        const long long base = a.off0 + (long long)i + (long long)j * a.sy + (long long)k * a.sz;
+        for (int slot = 0; slot < 6; ++slot) {
+            const int side = slot / 3, gl = slot % 3 + 1;
+            int bc = side == 0 ? a.bc_lo : a.bc_hi;
+            if (bc == BC_DMR_BOTTOM) {
+                const double x = a.lo0 + (i + 0.5) * a.dx0;
+                bc = x < 1.0 / 6.0 ? BC_INFLOW : BC_REFLECT;
+            } else if (bc == BC_DMR_TOP) {
+                bc = BC_INFLOW;
+            }
+            if (bc == BC_INFLOW) continue;
+            int src;
+            if (bc == BC_TRANSMISSIVE) src = side == 0 ? 0 : nd - 1;
+            else if (bc == BC_REFLECT) src = side == 0 ? gl - 1 : nd - gl;
+            else src = side == 0 ? nd - gl : gl - 1;
+            const long long g = base + (long long)src * sd;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                T val = ghost[(ln * 6 + slot) * NV + v];
+                if (bc == BC_REFLECT && v == 1 + d) val = -val;
+                G[g + v * a.sv] += val;
+            }
+        }
+    }
+}
+
+}  // namespace wis

@@ -41,6 +41,8 @@ struct weno_ctx {
     void* rhs_in = nullptr;
     void* rhs_out = nullptr;
     void* stage_io = nullptr;   // interior-size staging for host copies
+    void* vjp_w = nullptr;      // ghosted cotangent (ghost layers stay zero)
+    void* vjp_ghost = nullptr;  // per-line ghost-cell gradients
     DevTime* tm = nullptr;
     DevTime* tm_host = nullptr; // pinned
     unsigned long long* wcount = nullptr;
@@ -250,6 +252,8 @@ static void free_all(weno_ctx* c)
     if (c->rhs_in) cudaFree(c->rhs_in);
     if (c->rhs_out) cudaFree(c->rhs_out);
     if (c->stage_io) cudaFree(c->stage_io);
+    if (c->vjp_w) cudaFree(c->vjp_w);
+    if (c->vjp_ghost) cudaFree(c->vjp_ghost);
     if (c->tm) cudaFree(c->tm);
     if (c->tm_host) cudaFreeHost(c->tm_host);
     if (c->wcount) cudaFree(c->wcount);
@@ -487,6 +491,56 @@ weno_status weno_face_flags(weno_ctx* ctx, const void* U_dev, double t, uint8_t*
     if (st != WENO_OK) return st;
     CK(do_pack(ctx, U_dev, ctx->rhs_in, 1, ctx->stream));
     return issue_rhs(ctx, t, flags_dev);
+}
+
+weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, void* gU_dev, double t)
+{
+    if (!ctx || !U_dev || !w_dev || !gU_dev) return WENO_ERR_INVALID_ARG;
+    weno_status st = ensure_rhs_bufs(ctx);
+    if (st != WENO_OK) return st;
+    const size_t bytes = ctx->buf_elems * ctx->esz;
+    if (!ctx->vjp_w) {
+        CK(cudaMalloc(&ctx->vjp_w, bytes));
+        CK(cudaMemsetAsync(ctx->vjp_w, 0, bytes, ctx->stream));
+    }
+    if (!ctx->vjp_ghost) {
+        long long lines = 0;
+        for (int d = 0; d < ctx->dim; ++d) {
+            long long l = 1;
+            for (int k = 0; k < 3; ++k)
+                if (k != d) l *= ctx->n[k];
+            if (l > lines) lines = l;
+        }
+        CK(cudaMalloc(&ctx->vjp_ghost, (size_t)lines * 6 * ctx->nv * ctx->esz));
+    }
+    CK(do_pack(ctx, U_dev, ctx->rhs_in, 1, ctx->stream));
+    CK(do_pack(ctx, w_dev, ctx->vjp_w, 1, ctx->stream));
+    for (int d = 0; d < ctx->dim; ++d) {
+        wis::GhostArgs ga = ghost_args(ctx, ctx->rhs_in, d);
+        ga.t_fixed = t;
+        CK(do_ghost(ctx, ga, ctx->stream));
+    }
+    const bool f64 = ctx->prec == WENO_FP64;
+    for (int d = 0; d < ctx->dim; ++d) {
+        wis::VjpArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.U = ctx->rhs_in;
+        a.W = ctx->vjp_w;
+        a.G = ctx->rhs_out;
+        a.ghost = ctx->vjp_ghost;
+        a.accumulate = d > 0;
+        for (int k = 0; k < 3; ++k) a.n[k] = ctx->n[k];
+        a.sy = ctx->sy; a.sz = ctx->sz; a.sv = ctx->sv; a.off0 = ctx->off0;
+        a.inv_dx = ctx->inv_dx[d];
+        a.eps_h = ctx->eps_h[d];
+        a.gamma = ctx->p.gamma; a.eps = ctx->p.eps; a.c_lambda = ctx->p.c_lambda; a.hybrid = ctx->p.hybrid;
+        CK(f64 ? wis::vjp_f64(ctx->dim, d, a, ctx->stream) : wis::vjp_f32(ctx->dim, d, a, ctx->stream));
+        wis::GhostArgs ga = ghost_args(ctx, ctx->rhs_out, d);
+        CK(f64 ? wis::ghost_adj_f64(ctx->dim, ga, ctx->vjp_ghost, ctx->rhs_out, ctx->stream)
+               : wis::ghost_adj_f32(ctx->dim, ga, ctx->vjp_ghost, ctx->rhs_out, ctx->stream));
+    }
+    CK(do_pack(ctx, ctx->rhs_out, gU_dev, 0, ctx->stream));
+    return WENO_OK;
 }
 
 static weno_status finish_steps(weno_ctx* ctx)

@@ -20,4 +20,13 @@ cudaError_t pack_f32(const void* src, void* dst, int nv, const int* n, long long
     return launch_pack_t<float>(src, dst, nv, n, sy, sz, sv, off0, to_ghosted, nsm, s);
 }
 
+cudaError_t vjp_f32(int dim, int dir, const VjpArgs& a, cudaStream_t s)
+{
+    return launch_vjp_t<float>(dim, dir, a, s);
+}
+cudaError_t ghost_adj_f32(int dim, const GhostArgs& a, const void* ghost, void* G, cudaStream_t s)
+{
+    return launch_ghost_adj_t<float>(dim, a, ghost, G, s);
+}
+
 }  // namespace wis

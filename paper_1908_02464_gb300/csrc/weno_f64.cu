@@ -19,4 +19,13 @@ cudaError_t pack_f64(const void* src, void* dst, int nv, const int* n, long long
     return launch_pack_t<double>(src, dst, nv, n, sy, sz, sv, off0, to_ghosted, nsm, s);
 }
 
+cudaError_t vjp_f64(int dim, int dir, const VjpArgs& a, cudaStream_t s)
+{
+    return launch_vjp_t<double>(dim, dir, a, s);
+}
+cudaError_t ghost_adj_f64(int dim, const GhostArgs& a, const void* ghost, void* G, cudaStream_t s)
+{
+    return launch_ghost_adj_t<double>(dim, a, ghost, G, s);
+}
+
 }  // namespace wis

@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 
+#include "weno_adjoint.cuh"
 #include "weno_kernels.cuh"
 
 namespace wis {
@@ -123,7 +124,55 @@ cudaError_t launch_pack_t(const void* src, void* dst, int nv, const int* n, long
     return cudaGetLastError();
 }
 
+template <typename T, int DIM, int DIR>
+cudaError_t launch_vjp_one(const VjpArgs& a, cudaStream_t s)
+{
+    using SM = VjpSmem<T, DIM>;
+    auto kern = k_vjp<T, DIM, DIR>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int e0, e1;
+    if (DIR == 0) { e0 = a.n[1]; e1 = a.n[2]; }
+    else if (DIR == 1) { e0 = a.n[0]; e1 = a.n[2]; }
+    else { e0 = a.n[0]; e1 = a.n[1]; }
+    dim3 grid((a.n[DIR] + SM::SEG - 1) / SM::SEG, e0, e1);
+    kern<<<grid, VjpTile<DIM>::NT, SM::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_vjp_t(int dim, int dir, const VjpArgs& a, cudaStream_t s)
+{
+    if (dim == 1) return launch_vjp_one<T, 1, 0>(a, s);
+    if (dim == 2) return dir == 0 ? launch_vjp_one<T, 2, 0>(a, s) : launch_vjp_one<T, 2, 1>(a, s);
+    if (dir == 0) return launch_vjp_one<T, 3, 0>(a, s);
+    if (dir == 1) return launch_vjp_one<T, 3, 1>(a, s);
+    return launch_vjp_one<T, 3, 2>(a, s);
+}
+
+template <typename T>
+cudaError_t launch_ghost_adj_t(int dim, const GhostArgs& a, const void* ghost, void* G, cudaStream_t s)
+{
+    long long P;
+    if (a.dir == 0) P = (long long)a.n[1] * a.n[2];
+    else if (a.dir == 1) P = (long long)a.n[0] * a.n[2];
+    else P = (long long)a.n[0] * a.n[1];
+    const int blocks = grid_for(P, 256, 4096);
+    if (dim == 1) k_ghost_adj<T, 1><<<blocks, 256, 0, s>>>(a, ghost, G);
+    else if (dim == 2) k_ghost_adj<T, 2><<<blocks, 256, 0, s>>>(a, ghost, G);
+    else k_ghost_adj<T, 3><<<blocks, 256, 0, s>>>(a, ghost, G);
+    return cudaGetLastError();
+}
+
 // per-precision entry points (one translation unit each)
+cudaError_t vjp_f64(int dim, int dir, const VjpArgs& a, cudaStream_t s);
+cudaError_t vjp_f32(int dim, int dir, const VjpArgs& a, cudaStream_t s);
+cudaError_t ghost_adj_f64(int dim, const GhostArgs& a, const void* ghost, void* G, cudaStream_t s);
+cudaError_t ghost_adj_f32(int dim, const GhostArgs& a, const void* ghost, void* G, cudaStream_t s);
 cudaError_t sweep_f64(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);
 cudaError_t sweep_f32(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);
 cudaError_t sweep_mixed(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);

@@ -62,6 +62,7 @@ SIGNATURES = {
     "weno_get_state": (ctypes.c_int, [_vp, _vp, _ip, _dp]),
     "weno_rhs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double]),
     "weno_face_flags": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp]),
+    "weno_rhs_vjp": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double]),
     "weno_step": (ctypes.c_int, [_vp, ctypes.c_double, _dp]),
     "weno_advance": (ctypes.c_int, [_vp, ctypes.c_double, _ip, ctypes.POINTER(_ip)]),
     "weno_conserved_totals": (ctypes.c_int, [_vp, _dp]),
@@ -159,6 +160,10 @@ def weno_get_state(ctx: int, out) -> float:
 
 def weno_rhs(ctx: int, U_dev, dUdt_dev, t: float = 0.0) -> None:
     _check(load().weno_rhs(_vp(ctx), _vp(_ptr(U_dev)), _vp(_ptr(dUdt_dev)), float(t)), _vp(ctx))
+
+
+def weno_rhs_vjp(ctx: int, U_dev, w_dev, gU_dev, t: float = 0.0) -> None:
+    _check(load().weno_rhs_vjp(_vp(ctx), _vp(_ptr(U_dev)), _vp(_ptr(w_dev)), _vp(_ptr(gU_dev)), float(t)), _vp(ctx))
 
 
 def weno_face_flags(ctx: int, U_dev, t: float, flags_dev) -> None:
@@ -332,6 +337,16 @@ class Solver:
         weno_rhs(self.ctx, U_dev, out, t)
         return out
 
+    def rhs_vjp(self, U_dev, w_dev, t: float = 0.0, out=None):
+        """(d RHS / d U)^T w at U (flags and LLF argmax held fixed)."""
+        import torch
+        U_dev = U_dev.to(self.dtype).contiguous()
+        w_dev = w_dev.to(self.dtype).contiguous()
+        if out is None:
+            out = torch.empty_like(U_dev)
+        weno_rhs_vjp(self.ctx, U_dev, w_dev, out, t)
+        return out
+
     def face_flags(self, U_dev, t: float = 0.0):
         import torch
         U_dev = U_dev.to(self.dtype).contiguous()
@@ -480,3 +495,40 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- autograd
+
+def _make_rhs_function():
+    import torch
+
+    class RhsFunction(torch.autograd.Function):
+        """dU/dt = RHS(U) with a hand-written backward (weno_rhs_vjp): the
+        backward pass recomputes the nonlinear weights instead of storing
+        them."""
+
+        @staticmethod
+        def forward(ctx, U, solver, t):
+            ctx.solver = solver
+            ctx.t = float(t)
+            ctx.save_for_backward(U)
+            return solver.rhs(U.detach(), t)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (U,) = ctx.saved_tensors
+            g = ctx.solver.rhs_vjp(U.detach(), grad_out.contiguous(), ctx.t)
+            return g.to(U.dtype), None, None
+
+    return RhsFunction
+
+
+_RhsFunction = None
+
+
+def rhs_autograd(solver: "Solver", U, t: float = 0.0):
+    """Differentiable semi-discrete operator for torch autograd."""
+    global _RhsFunction
+    if _RhsFunction is None:
+        _RhsFunction = _make_rhs_function()
+    return _RhsFunction.apply(U, solver, t)

@@ -1,0 +1,144 @@
+"""Hand-written adjoint of the semi-discrete operator (weno_rhs_vjp) against
+the oracle's dual-number Jacobian-vector product (same flags and LLF argmax:
+<w, J v> = <J^T w, v> and full J^T w on small grids) and against FP64 central
+differences of the GPU forward operator where no flag changes."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1908_02464_gb300 import problems as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1908_02464_gb300 import weno  # noqa: E402
+
+
+def _vjp(prob, U, w, precision="fp64", t=0.0):
+    s = weno.Solver(prob, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    g = s.rhs_vjp(torch.from_numpy(U).to("cuda", dt), torch.from_numpy(w).to("cuda", dt), t)
+    torch.cuda.synchronize()
+    out = g.double().cpu().numpy()
+    s.close()
+    return out
+
+
+def _scale(U):
+    return np.abs(U).mean(axis=tuple(range(1, U.ndim)), keepdims=True)
+
+
+CASES = [(1, [40], "mixed"), (1, [33], "jumps"), (2, [30, 17], "mixed"), (2, [24, 19], "smooth"),
+         (3, [13, 11, 9], "mixed"), (3, [12, 9, 8], "jumps")]
+
+
+@pytest.mark.parametrize("dim,n,kind", CASES)
+def test_vjp_dot_product_identity_against_oracle_jvp(dim, n, kind):
+    """Bar: 1e-11 relative, or ten times the oracle's own change of <w, J v>
+    under one-ulp input perturbations where that is larger: the derivative of
+    the weights with respect to lambda scales like tau / (lambda beta + eps)^2
+    with eps = 1e-20, so on faces where lambda beta ~ eps the Jacobian itself
+    is ill-conditioned (the forward bar has the same reading)."""
+    prob, U = P.random_state(dim, n, seed=31 + dim, kind=kind)
+    rng = np.random.default_rng(7)
+    prng = np.random.default_rng(99)
+    w = rng.normal(size=U.shape)
+    g = _vjp(prob, U, w)
+    for _ in range(3):
+        v = rng.normal(size=U.shape) * _scale(U)
+        _, jv = orc.rhs_jvp(prob, U, v)
+        lhs, rhs = np.sum(w * jv), np.sum(g * v)
+        ref = np.sum(np.abs(w * jv))
+        tol = 1e-11 * ref
+        if abs(lhs - rhs) > tol:
+            kappa = 0.0
+            for _ in range(3):
+                Up = U * (1.0 + 2.220446049250313e-16 * prng.choice([-1.0, 0.0, 1.0], size=U.shape))
+                _, jv2 = orc.rhs_jvp(prob, Up, v)
+                kappa = max(kappa, abs(np.sum(w * jv2) - lhs))
+            tol = max(tol, 10.0 * kappa)
+        assert abs(lhs - rhs) <= tol, (lhs, rhs, tol)
+
+
+@pytest.mark.parametrize("dim,n,bcs", [(1, [16], (0, 0)), (1, [16], (1, 1)), (2, [9, 7], (2, 2)),
+                                      (2, [9, 8], (0, 1))])
+def test_vjp_equals_full_transposed_jacobian(dim, n, bcs):
+    """Every column of J from the oracle's JVP with unit tangents."""
+    prob, U = P.random_state(dim, n, seed=4, kind="mixed")
+    prob["bc_lo"] = [bcs[0]] * dim
+    prob["bc_hi"] = [bcs[1]] * dim
+    rng = np.random.default_rng(3)
+    w = rng.normal(size=U.shape)
+    g = _vjp(prob, U, w)
+    ref = np.zeros(U.size)
+    for k in range(U.size):
+        e = np.zeros(U.size)
+        e[k] = 1.0
+        _, jv = orc.rhs_jvp(prob, U, e.reshape(U.shape))
+        ref[k] = np.sum(w * jv)
+    assert np.allclose(g.reshape(-1), ref, rtol=1e-10, atol=1e-11 * np.max(np.abs(ref)))
+
+
+def test_vjp_double_mach_boundaries():
+    """Inflow, DMR bottom (inflow / wall) and top (moving shock) ghosts."""
+    prob, U = P.double_mach(40, 12)
+    rng = np.random.default_rng(5)
+    w = rng.normal(size=U.shape)
+    g = _vjp(prob, U, w, t=0.01)
+    for _ in range(2):
+        v = rng.normal(size=U.shape) * _scale(U)
+        _, jv = orc.rhs_jvp(prob, U, v, 0.01)
+        assert abs(np.sum(w * jv) - np.sum(g * v)) <= 1e-11 * np.sum(np.abs(w * jv))
+
+
+def test_vjp_against_central_differences_vortex_32():
+    """3D periodic vortex on a 32^3 grid: FP64 central differences of the GPU
+    forward operator along random directions (flags unchanged under +-h)."""
+    prob, U = P.vortex3d(32)
+    s = weno.Solver(prob, "fp64")
+    rng = np.random.default_rng(11)
+    w = rng.normal(size=U.shape)
+    Ud = torch.from_numpy(U).cuda()
+    g = s.rhs_vjp(Ud, torch.from_numpy(w).cuda()).cpu().numpy()
+    f0 = s.face_flags(Ud).cpu().numpy()
+    checked = 0
+    for _ in range(4):
+        v = rng.normal(size=U.shape) * _scale(U)
+        h = 1e-6
+        Up = torch.from_numpy(U + h * v).cuda()
+        Um = torch.from_numpy(U - h * v).cuda()
+        if not (np.array_equal(s.face_flags(Up).cpu().numpy(), f0) and
+                np.array_equal(s.face_flags(Um).cpu().numpy(), f0)):
+            continue
+        fd = np.sum(w * (s.rhs(Up).cpu().numpy() - s.rhs(Um).cpu().numpy())) / (2 * h)
+        assert abs(fd - np.sum(g * v)) <= 1e-6 * np.sum(np.abs(w * v)) * 1e2, (fd, np.sum(g * v))
+        checked += 1
+    assert checked >= 2
+    s.close()
+
+
+def test_autograd_function_matches_vjp():
+    prob, U = P.random_state(2, [20, 16], seed=2, kind="mixed")
+    s = weno.Solver(prob, "fp64")
+    Ut = torch.from_numpy(U).cuda().requires_grad_(True)
+    rng = np.random.default_rng(1)
+    w = torch.from_numpy(rng.normal(size=U.shape)).cuda()
+    r = weno.rhs_autograd(s, Ut)
+    (r * w).sum().backward()
+    g = s.rhs_vjp(Ut.detach(), w)
+    assert torch.equal(Ut.grad, g)
+    assert torch.equal(r.detach(), s.rhs(Ut.detach()))
+    s.close()
+
+
+def test_fp32_vjp_close_to_fp64():
+    prob, U = P.random_state(3, [16, 12, 10], seed=6, kind="smooth")
+    rng = np.random.default_rng(2)
+    w = rng.normal(size=U.shape)
+    g64 = _vjp(prob, U, w, "fp64")
+    g32 = _vjp(prob, U, w, "fp32")
+    rel = np.max(np.abs(g32 - g64)) / np.max(np.abs(g64))
+    assert rel < 1e-3, rel
