@@ -121,6 +121,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value: float, device=None) -> float:
+    """Max of a per-rank timing over all ranks (the slowest rank sets the
+    aggregate rate); the identity on a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(count: int, rank: int, world: int):
+    """Instances of a batch of independent problems owned by one rank."""
+    return list(range(rank, count, world))
+
+
 def sweep_flops(dim: int, n, weno_faces: int, d: int) -> float:
     fc, fu, fw = ALG_FLOPS[dim]
     cells = float(np.prod(n))
@@ -181,11 +198,7 @@ def run_ours(args) -> dict:
         return ms, wf
 
     ms64, wf64 = timed(s64, args.steps, args.warmup)
-    tot = sum(ms64)
-    if ws > 1:
-        t = torch.tensor([tot], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot = float(t.item())
+    tot = max_over_ranks(sum(ms64), device="cuda")
     value = ws * 3.0 * cells * args.steps / (tot * 1e-3)
     U64, t64 = s64.get_state()
     n_faces_step = 3 * ((NX + 1) * NY + NX * (NY + 1))
@@ -260,6 +273,7 @@ def run_ours(args) -> dict:
     s64.close()
 
     batch = None if args.no_batch else batched_riemann(args)
+    vortex = None if args.no_vortex else vortex3d_rhs_vjp(args)
 
     launches_per_step = 3 + 3 * 2 * 2 + 1   # cfl, dt, post, 3 x (2 ghosts + 2 sweeps), set_tend
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -276,6 +290,8 @@ def run_ours(args) -> dict:
     res.update(extra)
     if batch is not None:
         res["batched_riemann"] = batch
+    if vortex is not None:
+        res["vortex3d_256"] = vortex
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
     if ws > 1:
@@ -322,6 +338,63 @@ def batched_riemann(args) -> dict:
             entry["l1_rho_vs_fp64_max"] = float(np.max(l1))
         out[prec] = entry
         b.close()
+    return out
+
+
+def vortex3d_rhs_vjp(args) -> dict:
+    """3D periodic vortex on 256^3: forward RHS, one RK3 step and the
+    vector-Jacobian product of the RHS for a seeded N(0,1) cotangent."""
+    import torch
+    from paper_1908_02464_gb300 import problems as P
+    from paper_1908_02464_gb300 import weno
+    n = args.vortex_n
+    prob, U = P.vortex3d(n)
+    cells = n ** 3
+    gen = torch.Generator(device="cpu").manual_seed(1)
+    w = torch.randn(U.shape, generator=gen, dtype=torch.float64)
+    out = {"grid": [n, n, n], "cells": cells,
+           "workload": "rho=1, u=sin x cos y cos z, v=-cos x sin y cos z, w=0, p=100+(cos 2x+cos 2y)(cos 2z+2)/16 "
+                       "on [0,2pi]^3 periodic; cotangent N(0,1) seed 1"}
+    flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")
+    g64 = None
+    for prec in ("fp64", "fp32"):
+        s = weno.Solver(prob, prec)
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        Ud = torch.from_numpy(U).to("cuda", dt)
+        wd = w.to("cuda", dt)
+        r = s.rhs(Ud)
+        g = s.rhs_vjp(Ud, wd)
+
+        def timeit(fn, reps=3):
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return min(ts)
+
+        ms_rhs = timeit(lambda: s.rhs(Ud, 0.0, out=r))
+        ms_vjp = timeit(lambda: s.rhs_vjp(Ud, wd, 0.0, out=g))
+        s.set_state(Ud)
+        s.autotune(2)
+        s.enqueue_steps(10.0, 1)
+        torch.cuda.synchronize()
+        ms_step = timeit(lambda: s.enqueue_steps(10.0, 1))
+        entry = {"rhs_ms": ms_rhs, "rhs_cell_updates_per_s": cells / (ms_rhs * 1e-3),
+                 "step_ms": ms_step, "step_cell_updates_per_s": 3 * cells / (ms_step * 1e-3),
+                 "vjp_ms": ms_vjp, "vjp_cells_per_s": cells / (ms_vjp * 1e-3)}
+        gh = g.double().cpu()
+        if prec == "fp64":
+            g64 = gh
+        else:
+            entry["vjp_rel_err_vs_fp64"] = float((gh - g64).abs().max() / g64.abs().max())
+        out[prec] = entry
+        s.close()
+        del Ud, r, g
     return out
 
 
@@ -381,6 +454,8 @@ def main():
     ap.add_argument("--sweep-reps", type=int, default=5)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--no-vortex", action="store_true")
+    ap.add_argument("--vortex-n", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
