@@ -88,11 +88,17 @@ typedef struct {
     int alpha_thr;     /* alpha of Eq. eq31 (integer power)                      */
     int hybrid;        /* 1: linear upwind scheme where sigma^s < eps_h for all s */
     int precision;     /* weno_precision                                         */
+    int weights;       /* 0 regularized (Eq. eq8-r, the method), 1 WENO-IS
+                          (Eq. eq8), 2 WENO-IS of Wang et al. (Eq. eq14-15),
+                          3 optimal linear weights d_k                          */
+    int splitting;     /* 0 local LF over the six stencil cells, 1 global LF
+                          over the domain, 2 Roe (Eq. flxuspliting)              */
 } weno_params;
 
 typedef struct weno_ctx weno_ctx;
 
-/* Fill *p with the paper's constants and WENO_FP64. */
+/* Fill *p with the paper's constants, WENO_FP64, the regularized weights and
+ * LLF splitting. */
 weno_status weno_default_params(weno_params* p);
 
 /* Create a context on the current CUDA device.  Allocates the state buffers
@@ -137,7 +143,8 @@ weno_status weno_rhs(weno_ctx* ctx, const void* U_dev, void* dUdt_dev, double t)
  * conditions (fixed inflow states receive none).  U_dev, w_dev, gU_dev:
  * interior-only device arrays of the state's shape and element type.
  * Deterministic (no atomics).  Asynchronous; WENO_ERR_CUDA if a launch or
- * an allocation of the backward buffers fails. */
+ * an allocation of the backward buffers fails; WENO_ERR_UNSUPPORTED unless
+ * the context uses the regularized weights with LLF splitting. */
 weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, void* gU_dev, double t);
 
 /* Per-face hybrid flags of U_dev at time t: 1 where the linear upwind scheme

@@ -43,6 +43,7 @@ struct weno_ctx {
     void* stage_io = nullptr;   // interior-size staging for host copies
     void* vjp_w = nullptr;      // ghosted cotangent (ghost layers stay zero)
     void* vjp_ghost = nullptr;  // per-line ghost-cell gradients
+    unsigned long long* alpha_g = nullptr;   // global LF speeds [stage 0..3][dir][3]
     DevTime* tm = nullptr;
     DevTime* tm_host = nullptr; // pinned
     unsigned long long* wcount = nullptr;
@@ -104,6 +105,8 @@ static wis::SweepArgs sweep_args(weno_ctx* c, int dir)
     a.eps = c->p.eps;
     a.c_lambda = c->p.c_lambda;
     a.hybrid = c->p.hybrid;
+    a.wmode = c->p.weights;
+    a.split = c->p.splitting;
     a.weno_count = c->wcount;
     a.inv_dx_f = (float)a.inv_dx;
     a.gamma_f = (float)a.gamma;
@@ -138,10 +141,30 @@ static wis::GhostArgs ghost_args(weno_ctx* c, void* U, int dir)
     return a;
 }
 
+// global LF speeds of `in` into slot `slot` (zeroed first)
+static cudaError_t issue_lf(weno_ctx* c, const void* in, int slot, DevTime* tm, cudaStream_t s)
+{
+    unsigned long long* out = c->alpha_g + slot * 9;
+    cudaError_t e = cudaMemsetAsync(out, 0, 9 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    wis::CflArgs ca;
+    std::memset(&ca, 0, sizeof(ca));
+    ca.U = in;
+    for (int k = 0; k < 3; ++k) ca.n[k] = c->n[k];
+    ca.sy = c->sy; ca.sz = c->sz; ca.sv = c->sv; ca.off0 = c->off0;
+    ca.gamma = c->p.gamma;
+    ca.tm = tm;
+    return c->prec == WENO_FP64 ? wis::lf_f64(c->dim, ca, out, c->nsm, s) : wis::lf_f32(c->dim, ca, out, c->nsm, s);
+}
+
 // one RK stage: ghosts of `in` at the stage time, then the sweeps
 static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* out, double ra, double rb,
-                               double stage_c, cudaStream_t s)
+                               double stage_c, int slot, cudaStream_t s)
 {
+    if (c->p.splitting == wis::SPLIT_LF) {
+        cudaError_t e = issue_lf(c, in, slot, c->tm, s);
+        if (e != cudaSuccess) return e;
+    }
     for (int d = 0; d < c->dim; ++d) {
         wis::GhostArgs ga = ghost_args(c, in, d);
         ga.tm = c->tm;
@@ -153,6 +176,7 @@ static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* ou
         wis::SweepArgs a = sweep_args(c, d);
         a.U = in;
         a.tm = c->tm;
+        a.alpha_g = c->alpha_g + slot * 9 + 3 * d;
         if (d == c->dim - 1) {
             a.mode = wis::MODE_COMBINE;
             a.Un = base;
@@ -185,9 +209,9 @@ static cudaError_t issue_step(weno_ctx* c, int ph, cudaStream_t s)
     if (e != cudaSuccess) return e;
     wis::k_dt<<<1, 1, 0, s>>>(c->tm, c->p.cfl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = issue_stage(c, cur, nullptr, x, 0.0, 1.0, 0.0, s)) != cudaSuccess) return e;
-    if ((e = issue_stage(c, x, cur, y, 0.75, 0.25, 1.0, s)) != cudaSuccess) return e;
-    if ((e = issue_stage(c, y, cur, x, 1.0 / 3.0, 2.0 / 3.0, 0.5, s)) != cudaSuccess) return e;
+    if ((e = issue_stage(c, cur, nullptr, x, 0.0, 1.0, 0.0, 0, s)) != cudaSuccess) return e;
+    if ((e = issue_stage(c, x, cur, y, 0.75, 0.25, 1.0, 1, s)) != cudaSuccess) return e;
+    if ((e = issue_stage(c, y, cur, x, 1.0 / 3.0, 2.0 / 3.0, 0.5, 2, s)) != cudaSuccess) return e;
     wis::k_post<<<1, 1, 0, s>>>(c->tm);
     return cudaGetLastError();
 }
@@ -239,6 +263,8 @@ weno_status weno_default_params(weno_params* p)
     p->alpha_thr = 3;
     p->hybrid = 1;
     p->precision = WENO_FP64;
+    p->weights = 0;
+    p->splitting = 0;
     return WENO_OK;
 }
 
@@ -254,6 +280,7 @@ static void free_all(weno_ctx* c)
     if (c->stage_io) cudaFree(c->stage_io);
     if (c->vjp_w) cudaFree(c->vjp_w);
     if (c->vjp_ghost) cudaFree(c->vjp_ghost);
+    if (c->alpha_g) cudaFree(c->alpha_g);
     if (c->tm) cudaFree(c->tm);
     if (c->tm_host) cudaFreeHost(c->tm_host);
     if (c->wcount) cudaFree(c->wcount);
@@ -270,6 +297,10 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
     if (dim < 1 || dim > 3) { g_create_err = "dim must be 1, 2 or 3"; return WENO_ERR_INVALID_ARG; }
     if (params->precision < WENO_FP64 || params->precision > WENO_MIXED) {
         g_create_err = "unknown precision";
+        return WENO_ERR_INVALID_ARG;
+    }
+    if (params->weights < 0 || params->weights > 3 || params->splitting < 0 || params->splitting > 2) {
+        g_create_err = "unknown weights or splitting";
         return WENO_ERR_INVALID_ARG;
     }
     if (!(params->gamma > 1.0) || !(params->cfl > 0.0) || !(params->eps > 0.0) || params->alpha_thr < 0) {
@@ -342,6 +373,8 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
     ctx->tot_blocks = wis::grid_for(cells, 256, ctx->nsm * 4);
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->partial, sizeof(double) * ctx->tot_blocks * ctx->nv);
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->totals_dev, sizeof(double) * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->alpha_g, sizeof(unsigned long long) * 4 * 9);
+    if (e == cudaSuccess) e = cudaMemset(ctx->alpha_g, 0, sizeof(unsigned long long) * 4 * 9);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -451,10 +484,12 @@ static weno_status issue_rhs(weno_ctx* ctx, double t, uint8_t* flags)
         ga.t_fixed = t;
         CK(do_ghost(ctx, ga, ctx->stream));
     }
+    if (ctx->p.splitting == wis::SPLIT_LF) CK(issue_lf(ctx, ctx->rhs_in, 3, nullptr, ctx->stream));
     long long foff = 0;
     for (int d = 0; d < ctx->dim; ++d) {
         wis::SweepArgs a = sweep_args(ctx, d);
         a.U = ctx->rhs_in;
+        a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
         if (flags) a.flags = flags + foff;
         if (d == ctx->dim - 1) {
             a.mode = wis::MODE_RHS;
@@ -496,6 +531,10 @@ weno_status weno_face_flags(weno_ctx* ctx, const void* U_dev, double t, uint8_t*
 weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, void* gU_dev, double t)
 {
     if (!ctx || !U_dev || !w_dev || !gU_dev) return WENO_ERR_INVALID_ARG;
+    if (ctx->p.weights != 0 || ctx->p.splitting != wis::SPLIT_LLF) {
+        ctx->err = "the adjoint is implemented for the regularized weights with LLF splitting";
+        return WENO_ERR_UNSUPPORTED;
+    }
     weno_status st = ensure_rhs_bufs(ctx);
     if (st != WENO_OK) return st;
     const size_t bytes = ctx->buf_elems * ctx->esz;
@@ -624,6 +663,7 @@ static weno_status time_sweep_dir(weno_ctx* ctx, int d, int reps, void* flush_de
         CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
         wis::SweepArgs a = sweep_args(ctx, d);
         a.U = cur;
+        a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
         a.mode = wis::MODE_ACC_SET;
         a.acc = ctx->dim > 1 ? ctx->acc : ctx->rhs_out;
         CK(cudaEventRecord(e0, ctx->stream));
@@ -652,6 +692,7 @@ static weno_status prepare_timing(weno_ctx* ctx)
         ga.t_fixed = ctx->tm_host->t;
         CK(do_ghost(ctx, ga, ctx->stream));
     }
+    if (ctx->p.splitting == wis::SPLIT_LF) CK(issue_lf(ctx, cur, 3, nullptr, ctx->stream));
     return WENO_OK;
 }
 

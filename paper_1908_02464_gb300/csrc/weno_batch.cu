@@ -44,6 +44,7 @@ struct BatchArgs {
     int write_back;          // 0: trial run, the caller's states are not touched
     double gamma, cfl, eps, c_lambda, C_thr, L_char;
     int alpha_thr, hybrid, bc_lo, bc_hi;
+    int wmode, split;
 };
 
 template <int V> struct BatchTile;
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs b)
         a.inv_dx = 1.0 / dx;
         a.eps_h = eps_h;
         a.gamma = b.gamma; a.eps = b.eps; a.c_lambda = b.c_lambda; a.hybrid = b.hybrid;
+        a.wmode = b.wmode; a.split = b.split; a.alpha_g = nullptr;
         a.inv_dx_f = (float)a.inv_dx; a.gamma_f = (float)b.gamma; a.eps_f = (float)b.eps;
         a.lim0_f = (float)(3600.0 * eps_h); a.lam_scale_f = (float)(b.c_lambda * (1.0 / 3600.0));
         const T inv_dx_t[1] = {T(a.inv_dx)};
@@ -298,6 +300,7 @@ static BatchArgs batch_args(weno_batch* bt, void* U, int max_steps, int write_ba
     b.gamma = bt->p.gamma; b.cfl = bt->p.cfl; b.eps = bt->p.eps; b.c_lambda = bt->p.c_lambda;
     b.C_thr = bt->p.C_thr; b.L_char = bt->p.L_char; b.alpha_thr = bt->p.alpha_thr; b.hybrid = bt->p.hybrid;
     b.bc_lo = bt->bc_lo; b.bc_hi = bt->bc_hi;
+    b.wmode = bt->p.weights; b.split = bt->p.splitting;
     return b;
 }
 
@@ -345,9 +348,14 @@ weno_status weno_batch_create(const weno_batch_desc* d, const weno_params* param
         g_batch_err = "invalid batch description";
         return WENO_ERR_INVALID_ARG;
     }
-    if (params->precision < WENO_FP64 || params->precision > WENO_MIXED || d->max_steps < 0) {
-        g_batch_err = "invalid precision or max_steps";
+    if (params->precision < WENO_FP64 || params->precision > WENO_MIXED || d->max_steps < 0 ||
+        params->weights < 0 || params->weights > 3 || params->splitting < 0 || params->splitting > 2) {
+        g_batch_err = "invalid precision, weights, splitting or max_steps";
         return WENO_ERR_INVALID_ARG;
+    }
+    if (params->splitting == 1) {
+        g_batch_err = "global Lax-Friedrichs splitting is not available for batches (use LLF or Roe)";
+        return WENO_ERR_UNSUPPORTED;
     }
     for (int s = 0; s < 2; ++s) {
         const int bc = s == 0 ? d->bc_lo : d->bc_hi;

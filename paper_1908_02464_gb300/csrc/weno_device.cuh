@@ -199,20 +199,29 @@ __device__ __forceinline__ void back_proj_add(const Roe<T, DIM>& r, const T* w, 
 }
 
 // --------------------------------------------------- scalar reconstruction
+// Weight modes: 0 regularized (Eq. eq8-r, the method), 1 WENO-IS (Eq. eq8),
+// 2 WENO-IS of Wang et al. (Eq. eq14-15), 3 optimal linear weights d_k.
+enum { W_REG = 0, W_IS = 1, W_WANG = 2, W_LINEAR = 3 };
+
 // f0..f4 = f_{j-2} .. f_{j+2}; lam = c sigma^s (Eq. eq29).  Returns the
-// reconstructed value at x_{j+1/2} with the weights of Eq. eq8-r.
+// reconstructed value at x_{j+1/2}.  Every weight rule is written as
+// alpha_k = d_k (1 + LT_k / D_k):
+//   regularized: D_k = lam beta_k + E_k + eps, LT_k = lam tau_5
+//   WENO-IS:     D_k = beta_k + eps,            LT_k = tau_5
+//   Wang:        D_k = beta_k + eps,            LT_{0,1} = tau_5^2/(beta_01 + eps), LT_{2,3} = tau_5
 template <typename T>
-__device__ __forceinline__ T recon(T a, T b, T c, T d, T e, T lam, T eps);
+__device__ __forceinline__ T recon(T a, T b, T c, T d, T e, T lam, T eps, int wmode = W_REG);
 
 template <>
 __device__ __forceinline__ double recon<double>(double a, double b, double c, double d, double e,
-                                                double lam, double eps)
+                                                double lam, double eps, int wmode)
 {
     // Eq. eq6
     const double q0 = 0.5 * (c + d);
     const double q1 = fmaT(1.5, c, -0.5 * b);
     const double q2 = fmaT(1.0 / 3.0, c, fmaT(5.0 / 6.0, d, (-1.0 / 6.0) * e));
     const double q3 = fmaT(1.0 / 3.0, a, fmaT(-7.0 / 6.0, b, (11.0 / 6.0) * c));
+    if (wmode == W_LINEAR) return fmaT(0.4, q0, fmaT(0.2, q1, fmaT(0.3, q2, 0.1 * q3)));
     // Eq. eq11
     const double b0 = (d - c) * (d - c);
     const double b1 = (c - b) * (c - b);
@@ -225,22 +234,36 @@ __device__ __forceinline__ double recon<double>(double a, double b, double c, do
     t = fmaT(-4.0, b + d, a + e) + 6.0 * c;
     s = fmaT(2.0, b - d, e - a);
     const double tau = fmaT(13.0 / 12.0, t * t, 0.25 * (s * s));
-    // Eq. eq18 (E_2 = E_3 = 0)
-    t = fmaT(-2.0, c, b + d);
-    const double E = (t * t) * (1.0 / 45.0);
-    // Eq. eq8-r: alpha_k = d_k (D_k + lam tau)/D_k with D_k = lam beta_k + E_k + eps.
-    // The normalized sum sum_k alpha_k q_k / sum_k alpha_k is evaluated
-    // over the common denominator D_0 D_1 D_2 D_3 (one division).
-    const double D0 = fmaT(lam, b0, E + eps);
-    const double D1 = fmaT(lam, b1, E + eps);
-    const double D2 = fmaT(lam, b2, eps);
-    const double D3 = fmaT(lam, b3, eps);
-    const double lt = lam * tau;
+    double D0, D1, D2, D3, L01, L23;
+    if (wmode == W_REG) {
+        // Eq. eq18 (E_2 = E_3 = 0) and Eq. eq8-r
+        t = fmaT(-2.0, c, b + d);
+        const double E = (t * t) * (1.0 / 45.0);
+        D0 = fmaT(lam, b0, E + eps);
+        D1 = fmaT(lam, b1, E + eps);
+        D2 = fmaT(lam, b2, eps);
+        D3 = fmaT(lam, b3, eps);
+        L01 = L23 = lam * tau;
+    } else {
+        // Eq. eq8, and Eq. eq14-15 for the two-point stencils
+        D0 = b0 + eps; D1 = b1 + eps; D2 = b2 + eps; D3 = b3 + eps;
+        L23 = tau;
+        if (wmode == W_WANG) {
+            t = fmaT(-2.0, c, b + d);
+            s = b - d;
+            const double b01 = fmaT(13.0 / 12.0, t * t, 0.25 * (s * s));
+            L01 = tau * (tau / (b01 + eps));
+        } else {
+            L01 = tau;
+        }
+    }
+    // sum_k alpha_k q_k / sum_k alpha_k over the common denominator
+    // D_0 D_1 D_2 D_3 (one division)
     const double D01 = D0 * D1, D23 = D2 * D3;
-    const double w0 = 0.4 * (D0 + lt) * (D1 * D23);
-    const double w1 = 0.2 * (D1 + lt) * (D0 * D23);
-    const double w2 = 0.3 * (D2 + lt) * (D01 * D3);
-    const double w3 = 0.1 * (D3 + lt) * (D01 * D2);
+    const double w0 = 0.4 * (D0 + L01) * (D1 * D23);
+    const double w1 = 0.2 * (D1 + L01) * (D0 * D23);
+    const double w2 = 0.3 * (D2 + L23) * (D01 * D3);
+    const double w3 = 0.1 * (D3 + L23) * (D01 * D2);
     const double num = fmaT(w0, q0, fmaT(w1, q1, fmaT(w2, q2, w3 * q3)));
     const double den = (w0 + w1) + (w2 + w3);
     return num / den;
@@ -248,12 +271,13 @@ __device__ __forceinline__ double recon<double>(double a, double b, double c, do
 
 template <>
 __device__ __forceinline__ float recon<float>(float a, float b, float c, float d, float e,
-                                              float lam, float eps)
+                                              float lam, float eps, int wmode)
 {
     const float q0 = 0.5f * (c + d);
     const float q1 = fmaT(1.5f, c, -0.5f * b);
     const float q2 = fmaT(1.0f / 3.0f, c, fmaT(5.0f / 6.0f, d, (-1.0f / 6.0f) * e));
     const float q3 = fmaT(1.0f / 3.0f, a, fmaT(-7.0f / 6.0f, b, (11.0f / 6.0f) * c));
+    if (wmode == W_LINEAR) return fmaT(0.4f, q0, fmaT(0.2f, q1, fmaT(0.3f, q2, 0.1f * q3)));
     const float b0 = (d - c) * (d - c);
     const float b1 = (c - b) * (c - b);
     float t = fmaT(-2.0f, d, c) + e;
@@ -265,15 +289,33 @@ __device__ __forceinline__ float recon<float>(float a, float b, float c, float d
     t = fmaT(-4.0f, b + d, a + e) + 6.0f * c;
     s = fmaT(2.0f, b - d, e - a);
     const float tau = fmaT(13.0f / 12.0f, t * t, 0.25f * (s * s));
-    t = fmaT(-2.0f, c, b + d);
-    const float E = (t * t) * (1.0f / 45.0f);
     // In float the product of four denominators can underflow (eps = 1e-20),
-    // so each ratio lam tau / D_k takes its own reciprocal.
-    const float lt = lam * tau;
-    const float a0 = 0.4f * fmaT(lt, __fdividef(1.0f, fmaT(lam, b0, E + eps)), 1.0f);
-    const float a1 = 0.2f * fmaT(lt, __fdividef(1.0f, fmaT(lam, b1, E + eps)), 1.0f);
-    const float a2 = 0.3f * fmaT(lt, __fdividef(1.0f, fmaT(lam, b2, eps)), 1.0f);
-    const float a3 = 0.1f * fmaT(lt, __fdividef(1.0f, fmaT(lam, b3, eps)), 1.0f);
+    // so each ratio LT_k / D_k takes its own reciprocal.
+    float D0, D1, D2, D3, L01, L23;
+    if (wmode == W_REG) {
+        t = fmaT(-2.0f, c, b + d);
+        const float E = (t * t) * (1.0f / 45.0f);
+        D0 = fmaT(lam, b0, E + eps);
+        D1 = fmaT(lam, b1, E + eps);
+        D2 = fmaT(lam, b2, eps);
+        D3 = fmaT(lam, b3, eps);
+        L01 = L23 = lam * tau;
+    } else {
+        D0 = b0 + eps; D1 = b1 + eps; D2 = b2 + eps; D3 = b3 + eps;
+        L23 = tau;
+        if (wmode == W_WANG) {
+            t = fmaT(-2.0f, c, b + d);
+            s = b - d;
+            const float b01 = fmaT(13.0f / 12.0f, t * t, 0.25f * (s * s));
+            L01 = tau * __fdividef(tau, b01 + eps);
+        } else {
+            L01 = tau;
+        }
+    }
+    const float a0 = 0.4f * fmaT(L01, __fdividef(1.0f, D0), 1.0f);
+    const float a1 = 0.2f * fmaT(L01, __fdividef(1.0f, D1), 1.0f);
+    const float a2 = 0.3f * fmaT(L23, __fdividef(1.0f, D2), 1.0f);
+    const float a3 = 0.1f * fmaT(L23, __fdividef(1.0f, D3), 1.0f);
     const float num = fmaT(a0, q0, fmaT(a1, q1, fmaT(a2, q2, a3 * q3)));
     const float den = (a0 + a1) + (a2 + a3);
     return num / den;

@@ -29,4 +29,9 @@ cudaError_t ghost_adj_f32(int dim, const GhostArgs& a, const void* ghost, void* 
     return launch_ghost_adj_t<float>(dim, a, ghost, G, s);
 }
 
+cudaError_t lf_f32(int dim, const CflArgs& a, unsigned long long* out, int nsm, cudaStream_t s)
+{
+    return launch_lf_t<float>(dim, a, out, nsm, s);
+}
+
 }  // namespace wis

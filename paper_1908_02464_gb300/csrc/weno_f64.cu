@@ -28,4 +28,9 @@ cudaError_t ghost_adj_f64(int dim, const GhostArgs& a, const void* ghost, void* 
     return launch_ghost_adj_t<double>(dim, a, ghost, G, s);
 }
 
+cudaError_t lf_f64(int dim, const CflArgs& a, unsigned long long* out, int nsm, cudaStream_t s)
+{
+    return launch_lf_t<double>(dim, a, out, nsm, s);
+}
+
 }  // namespace wis

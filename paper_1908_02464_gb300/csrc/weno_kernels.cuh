@@ -34,6 +34,9 @@ struct DevTime {
 };
 
 enum { MODE_ACC_SET = 0, MODE_ACC_ADD = 1, MODE_COMBINE = 2, MODE_RHS = 3 };
+// flux splitting (Eq. flxuspliting): local LF over the six stencil cells,
+// global LF over the domain, Roe (the Roe-average eigenvalue)
+enum { SPLIT_LLF = 0, SPLIT_LF = 1, SPLIT_RF = 2 };
 
 struct SweepArgs {
     const void* U;      // stage input, ghosted layout
@@ -49,6 +52,9 @@ struct SweepArgs {
     long long sy, sz, sv, off0;
     double inv_dx, eps_h, gamma, eps, c_lambda;
     int hybrid;
+    int wmode;                      // W_REG, W_IS, W_WANG, W_LINEAR
+    int split;                      // SPLIT_LLF, SPLIT_LF, SPLIT_RF
+    const unsigned long long* alpha_g;  // SPLIT_LF: bits of max |u-c|, |u|, |u+c| of this direction
     // the same constants pre-rounded for float kernels (a double conversion
     // or division per thread would run on the slow FP64 pipe)
     float inv_dx_f, gamma_f, eps_f, lim0_f, lam_scale_f, rk_a_f, rk_b_f;
@@ -218,15 +224,27 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             bool smooth = a.hybrid != 0;
 #pragma unroll
             for (int s = 0; s < NV; ++s) smooth = smooth && lt_nn(w[s] * w[s], lim);
-            // LLF speeds: max over the six stencil cells
-            T am = cq[CL::LM * NCELL + cidx(l, p)];
-            T a0 = cq[CL::L0 * NCELL + cidx(l, p)];
-            T ap = cq[CL::LP * NCELL + cidx(l, p)];
+            // splitting speeds: LLF max over the six stencil cells, global
+            // LF maxima, or the Roe-average eigenvalues
+            T am, a0, ap;
+            if (a.split == SPLIT_LLF) {
+                am = cq[CL::LM * NCELL + cidx(l, p)];
+                a0 = cq[CL::L0 * NCELL + cidx(l, p)];
+                ap = cq[CL::LP * NCELL + cidx(l, p)];
 #pragma unroll
-            for (int m = 1; m < 6; ++m) {
-                am = max_nn(am, cq[CL::LM * NCELL + cidx(l, p + m)]);
-                a0 = max_nn(a0, cq[CL::L0 * NCELL + cidx(l, p + m)]);
-                ap = max_nn(ap, cq[CL::LP * NCELL + cidx(l, p + m)]);
+                for (int m = 1; m < 6; ++m) {
+                    am = max_nn(am, cq[CL::LM * NCELL + cidx(l, p + m)]);
+                    a0 = max_nn(a0, cq[CL::L0 * NCELL + cidx(l, p + m)]);
+                    ap = max_nn(ap, cq[CL::LP * NCELL + cidx(l, p + m)]);
+                }
+            } else if (a.split == SPLIT_RF) {
+                am = absT(r.u[DIR] - r.c);
+                a0 = absT(r.u[DIR]);
+                ap = absT(r.u[DIR] + r.c);
+            } else {
+                am = T(__longlong_as_double((long long)a.alpha_g[0]));
+                a0 = T(__longlong_as_double((long long)a.alpha_g[1]));
+                ap = T(__longlong_as_double((long long)a.alpha_g[2]));
             }
             if (smooth) {
                 // Eq. linearupwind: [central six-point flux + sum_s R^s alpha^s (60 dv^s)] / 60
@@ -341,8 +359,8 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             const T lam = fr[(FR::LAM + s) * NFACE + f];
             const T* v = fpm + ((q * NV + s) * 2 + sg) * 6;
             T out;
-            if (sg == 0) out = recon<T>(v[0], v[1], v[2], v[3], v[4], lam, eps);
-            else out = recon<T>(v[5], v[4], v[3], v[2], v[1], lam, eps);
+            if (sg == 0) out = recon<T>(v[0], v[1], v[2], v[3], v[4], lam, eps, a.wmode);
+            else out = recon<T>(v[5], v[4], v[3], v[2], v[1], lam, eps, a.wmode);
             res[(q * NV + s) * 2 + sg] = out;
         }
         __syncthreads();
@@ -606,6 +624,51 @@ __global__ void __launch_bounds__(256) k_cfl(CflArgs a)
             atomicMax(&a.tm->smax_bits, (unsigned long long)__double_as_longlong(v));
     }
     if (bad) atomicOr(&a.tm->status, 1);
+}
+
+// global Lax-Friedrichs speeds (Sec. 2.4 step (4), l = the whole domain):
+// per direction d, max over interior cells of |u_d - c|, |u_d|, |u_d + c|,
+// as bits of non-negative doubles (out[3 d + k], zeroed beforehand)
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_lf_alpha(CflArgs a, unsigned long long* out)
+{
+    constexpr int NV = DIM + 2;
+    if (a.tm != nullptr && (a.tm->status != 0 || !(a.tm->dt > 0.0))) return;
+    const T* U = reinterpret_cast<const T*>(a.U);
+    const long long nx = a.n[0], ny = a.n[1];
+    const long long total = nx * ny * (long long)a.n[2];
+    const T gamma = T(a.gamma), gm1 = gamma - T(1);
+    double mx[3 * DIM];
+#pragma unroll
+    for (int q = 0; q < 3 * DIM; ++q) mx[q] = 0.0;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+        const long long i = id % nx, j = (id / nx) % ny, k = id / (nx * ny);
+        const long long g = a.off0 + i + j * a.sy + k * a.sz;
+        T u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = U[g + v * a.sv];
+        T q[CellLayout<DIM>::NQ];
+        const T irho = Ar<T>::rcp(u[0]);
+        T ke2 = T(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) ke2 = fmaT(u[1 + d], u[1 + d] * irho, ke2);
+        const T p = gm1 * fmaT(T(-0.5), ke2, u[DIM + 1]);
+        const T c = Ar<T>::sqrt_(gamma * p * irho);
+        (void)q;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const T un = u[1 + d] * irho;
+            mx[3 * d + 0] = maxT(mx[3 * d + 0], (double)absT(un - c));
+            mx[3 * d + 1] = maxT(mx[3 * d + 1], (double)absT(un));
+            mx[3 * d + 2] = maxT(mx[3 * d + 2], (double)absT(un + c));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 3 * DIM; ++q) {
+        const double v = warp_max(mx[q]);
+        if ((threadIdx.x & 31) == 0 && v > 0.0) atomicMax(&out[q], (unsigned long long)__double_as_longlong(v));
+    }
 }
 
 // dt = CFL / smax clipped to t_end; resets the reduction cell

@@ -105,6 +105,17 @@ cudaError_t launch_cfl_t(int dim, const CflArgs& a, int nsm, cudaStream_t s)
 }
 
 template <typename T>
+cudaError_t launch_lf_t(int dim, const CflArgs& a, unsigned long long* out, int nsm, cudaStream_t s)
+{
+    const long long cells = (long long)a.n[0] * a.n[1] * a.n[2];
+    const int blocks = grid_for(cells, 256, nsm * 8);
+    if (dim == 1) k_lf_alpha<T, 1><<<blocks, 256, 0, s>>>(a, out);
+    else if (dim == 2) k_lf_alpha<T, 2><<<blocks, 256, 0, s>>>(a, out);
+    else k_lf_alpha<T, 3><<<blocks, 256, 0, s>>>(a, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_totals_t(int dim, const TotArgs& a, int blocks, cudaStream_t s)
 {
     if (dim == 1) k_totals<T, 1><<<blocks, 256, 0, s>>>(a);
@@ -180,6 +191,8 @@ cudaError_t ghost_f64(int dim, const GhostArgs& a, cudaStream_t s);
 cudaError_t ghost_f32(int dim, const GhostArgs& a, cudaStream_t s);
 cudaError_t cfl_f64(int dim, const CflArgs& a, int nsm, cudaStream_t s);
 cudaError_t cfl_f32(int dim, const CflArgs& a, int nsm, cudaStream_t s);
+cudaError_t lf_f64(int dim, const CflArgs& a, unsigned long long* out, int nsm, cudaStream_t s);
+cudaError_t lf_f32(int dim, const CflArgs& a, unsigned long long* out, int nsm, cudaStream_t s);
 cudaError_t totals_f64(int dim, const TotArgs& a, int blocks, cudaStream_t s);
 cudaError_t totals_f32(int dim, const TotArgs& a, int blocks, cudaStream_t s);
 cudaError_t pack_f64(const void* src, void* dst, int nv, const int* n, long long sy, long long sz, long long sv,

@@ -39,7 +39,12 @@ class weno_grid(ctypes.Structure):
 class weno_params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("eps", ctypes.c_double),
                 ("c_lambda", ctypes.c_double), ("C_thr", ctypes.c_double), ("L_char", ctypes.c_double),
-                ("alpha_thr", ctypes.c_int), ("hybrid", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("alpha_thr", ctypes.c_int), ("hybrid", ctypes.c_int), ("precision", ctypes.c_int),
+                ("weights", ctypes.c_int), ("splitting", ctypes.c_int)]
+
+
+WEIGHTS = {"reg": 0, "is": 1, "wang": 2, "linear": 3}
+SPLITTINGS = {"llf": 0, "lf": 1, "rf": 2}
 
 
 class weno_batch_desc(ctypes.Structure):
@@ -271,8 +276,8 @@ def make_params(problem: dict, precision: str = "fp64") -> weno_params:
         p.alpha_thr = int(problem["alpha_thr"])
     if "hybrid" in problem:
         p.hybrid = int(problem["hybrid"])
-    if problem.get("weights", "reg") != "reg" or problem.get("splitting", "llf") != "llf":
-        raise WenoError(WENO_ERR_UNSUPPORTED, "the CUDA path implements regularized weights with LLF splitting")
+    p.weights = WEIGHTS[problem.get("weights", "reg")]
+    p.splitting = SPLITTINGS[problem.get("splitting", "llf")]
     p.precision = PRECISIONS[precision]
     return p
 

@@ -65,9 +65,22 @@ def test_create_rejects_invalid_grids_without_touching_the_gpu():
         assert e.value.status == weno.WENO_ERR_INVALID_ARG
 
 
-def test_unsupported_variants_are_refused():
+def test_weight_and_splitting_codes_reach_the_params():
     from paper_1908_02464_gb300 import problems as P
     prob, _ = P.blast_waves(100)   # Roe splitting
+    p = weno.make_params(prob)
+    assert p.splitting == 2 and p.weights == 0
+    prob["weights"] = "wang"
+    prob["splitting"] = "lf"
+    p = weno.make_params(prob)
+    assert p.splitting == 1 and p.weights == 2
+
+
+def test_create_rejects_unknown_weight_rule():
+    from paper_1908_02464_gb300 import problems as P
+    prob, _ = P.sod(100)
+    p = weno.make_params(prob)
+    p.weights = 7
     with pytest.raises(weno.WenoError) as e:
-        weno.make_params(prob)
-    assert e.value.status == weno.WENO_ERR_UNSUPPORTED
+        weno.weno_create(weno.make_grid(prob), p)
+    assert e.value.status == weno.WENO_ERR_INVALID_ARG

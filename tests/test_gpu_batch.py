@@ -59,6 +59,33 @@ def test_batch_equals_single_problem_solver_bitwise(precision):
     b.close()
 
 
+@pytest.mark.parametrize("weights,splitting", [("reg", 2), ("is", 0), ("wang", 2)])
+def test_batch_variants_equal_single_solver(weights, splitting):
+    params, states = _small_batch(count=10, seed=13)
+    code = {"reg": 0, "is": 1, "wang": 2}[weights]
+    b = weno.Batch(params["N"], 0.0, 1.0, params["t_end"], "fp64", weights=code, splitting=splitting)
+    U = b.pack(states)
+    b.run(U)
+    st, steps, t = b.results()
+    out = b.unpack(U)
+    for i in range(b.count):
+        prob, Ui = P.riemann_instance(params, i)
+        prob["weights"] = weights
+        prob["splitting"] = {0: "llf", 2: "rf"}[splitting]
+        s = weno.Solver(prob, "fp64")
+        s.set_state(Ui)
+        sti = 0
+        try:
+            s.advance(prob["t_end"])
+        except weno.WenoError as e:
+            sti = e.status
+        V, ti = s.get_state()
+        assert st[i] == sti and t[i] == ti and steps[i] == s.time()[1]
+        assert np.array_equal(out[i], V)
+        s.close()
+    b.close()
+
+
 def test_batch_matches_oracle():
     params, states = _small_batch(count=6, seed=5)
     b = weno.Batch(params["N"], 0.0, 1.0, params["t_end"], "fp64")

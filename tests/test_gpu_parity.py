@@ -97,6 +97,48 @@ def test_rhs_parity_hybrid_off():
     assert frac == 0.0
 
 
+@pytest.mark.parametrize("weights", ["is", "wang", "linear"])
+@pytest.mark.parametrize("hybrid", [0, 1])
+def test_rhs_parity_comparator_weights(weights, hybrid):
+    """WENO-IS (Eq. eq8), Wang (Eq. eq14-15) and linear weights."""
+    prob, U = P.random_state(2, [61, 23], seed=71, kind="mixed")
+    prob["weights"] = weights
+    prob["hybrid"] = hybrid
+    _compare_rhs(prob, U)
+
+
+@pytest.mark.parametrize("splitting", ["rf", "lf"])
+@pytest.mark.parametrize("dim,n", [(1, [131]), (2, [70, 19]), (3, [20, 13, 11])])
+def test_rhs_parity_splittings(splitting, dim, n):
+    """Roe and global Lax-Friedrichs splitting (Eq. flxuspliting)."""
+    prob, U = P.random_state(dim, n, seed=72 + dim, kind="mixed")
+    prob["splitting"] = splitting
+    _compare_rhs(prob, U)
+
+
+@pytest.mark.parametrize("case", ["blast_rf", "blast_llf", "123", "shu_osher_is", "shu_osher_wang_lf"])
+def test_full_run_parity_variants(case):
+    """Two blast waves with Roe splitting and reflecting walls (Sec. 4.3),
+    the 123 problem, Shu-Osher with the comparator weights."""
+    if case.startswith("blast"):
+        prob, U = P.blast_waves(400)
+        prob["splitting"] = "rf" if case == "blast_rf" else "llf"
+    elif case == "123":
+        prob, U = P.problem_123(200)
+    else:
+        prob, U = P.shu_osher(400)
+        prob["t_end"] = 0.6
+        prob["weights"] = "is" if case == "shu_osher_is" else "wang"
+        if case.endswith("lf"):
+            prob["splitting"] = "lf"
+    Uo = U.copy()
+    st, to, ko = orc.advance(prob, Uo, 0.0, prob["t_end"])
+    assert st == 0
+    V, t, k = _run_gpu(prob, U)
+    assert t == to and k == ko
+    assert np.mean(np.abs(V[0] - Uo[0])) <= 1e-10
+
+
 def test_rhs_parity_boundaries():
     """Shock tubes (transmissive), blast waves with reflecting walls (LLF on
     the GPU path), double Mach reflection (inflow, DMR bottom/top at t>0)."""
