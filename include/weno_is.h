@@ -62,8 +62,10 @@ enum {
     WENO_BC_INFLOW = 3,       /* fixed conservative state bc_state[0]                 */
     WENO_BC_DMR_BOTTOM = 4,   /* y-low of the double Mach reflection (Sec. 4.5):
                                  bc_state[0] for x < 1/6, reflecting wall otherwise */
-    WENO_BC_DMR_TOP = 5       /* y-high of the double Mach reflection: bc_state[0]
+    WENO_BC_DMR_TOP = 5,      /* y-high of the double Mach reflection: bc_state[0]
                                  for x < 1/6 + (1 + 20 t)/sqrt(3), bc_state[1] else */
+    WENO_BC_JET = 6           /* x-low inflow jet (Sec. 4.7): bc_state[0] where
+                                 y < 0.05, bc_state[1] elsewhere                   */
 };
 
 /* Uniform cell-centred grid x_i = lo + (i + 1/2) dx (Sec. 2.1, x_j = j dx). */
@@ -86,7 +88,11 @@ typedef struct {
     double C_thr;      /* C of Eq. eq31                                          */
     double L_char;     /* L of Eq. eq31                                          */
     int alpha_thr;     /* alpha of Eq. eq31 (integer power)                      */
-    int hybrid;        /* 1: linear upwind scheme where sigma^s < eps_h for all s */
+    int hybrid;        /* 0: WENO everywhere; 1: linear upwind scheme on faces
+                          where sigma^s < eps_h for all s (Eq. eqhy, the
+                          method); 2: also per field on the other faces (the
+                          optimal linear weights for each field with
+                          sigma^s < eps_h)                                      */
     int precision;     /* weno_precision                                         */
     int weights;       /* 0 regularized (Eq. eq8-r, the method), 1 WENO-IS
                           (Eq. eq8), 2 WENO-IS of Wang et al. (Eq. eq14-15),
@@ -144,7 +150,8 @@ weno_status weno_rhs(weno_ctx* ctx, const void* U_dev, void* dUdt_dev, double t)
  * interior-only device arrays of the state's shape and element type.
  * Deterministic (no atomics).  Asynchronous; WENO_ERR_CUDA if a launch or
  * an allocation of the backward buffers fails; WENO_ERR_UNSUPPORTED unless
- * the context uses the regularized weights with LLF splitting. */
+ * the context uses the regularized weights with LLF splitting and hybrid
+ * 0 or 1. */
 weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, void* gU_dev, double t);
 
 /* Per-face hybrid flags of U_dev at time t: 1 where the linear upwind scheme

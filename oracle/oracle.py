@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BC_TRANSMISSIVE, BC_REFLECT, BC_PERIODIC, BC_INFLOW, BC_DMR_BOTTOM, BC_DMR_TOP = range(6)
+BC_TRANSMISSIVE, BC_REFLECT, BC_PERIODIC, BC_INFLOW, BC_DMR_BOTTOM, BC_DMR_TOP, BC_JET = range(7)
 WEIGHTS = {"reg": 0, "is": 1, "wang": 2, "linear": 3}
 SPLITTING = {"llf": 0, "lf": 1, "rf": 2}
 

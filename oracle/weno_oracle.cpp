@@ -67,7 +67,8 @@ typedef struct {
     double C_thr;         /* C of Eq. eq31 (1)                               */
     double L_char;        /* L of Eq. eq31 (1)                               */
     int alpha_thr;        /* alpha of Eq. eq31 (3)                           */
-    int hybrid;           /* 1: switch to the linear scheme on smooth faces  */
+    int hybrid;           /* 1: switch to the linear scheme on smooth faces;
+                             2: per field (linear weights where sigma^s < eps_h) */
     int weights;          /* 0 regularized (eq8-r), 1 WENO-IS (eq8),
                              2 WENO-IS Wang (eq14), 3 linear d_k             */
     int splitting;        /* 0 LLF, 1 global LF, 2 Roe                       */
@@ -78,7 +79,11 @@ typedef struct {
 }
 
 enum { BC_TRANSMISSIVE = 0, BC_REFLECT = 1, BC_PERIODIC = 2, BC_INFLOW = 3,
-       BC_DMR_BOTTOM = 4, BC_DMR_TOP = 5 };
+       BC_DMR_BOTTOM = 4, BC_DMR_TOP = 5, BC_JET = 6 };
+
+/* inflow jet (Mach 2000 jet of Sec. 4.7): bc_state[0] where y < JET_HALF_WIDTH,
+ * bc_state[1] elsewhere */
+static const double JET_HALF_WIDTH = 0.05;
 
 static const int NG = 3;  /* ghost layers */
 
@@ -426,12 +431,14 @@ static void face_flux(const or_cfg& cf, int d, double eps_h, const CellQ<R>* S,
             }
             /* Eq. eq29 */
             R lam = R(cf.c_lambda) * sigma[s];
+            /* per-field hybrid: the linear scheme for a smooth field */
+            const int wrule = (cf.hybrid == 2 && sigma[s] < R(eps_h)) ? 3 : cf.weights;
             /* Eq. reconstruction: positive part on j-2..j+2, negative part on
              * the mirrored sequence j+3..j-1 */
             R plus_in[5] = {fp[0], fp[1], fp[2], fp[3], fp[4]};
             R minus_in[5] = {fm[5], fm[4], fm[3], fm[2], fm[1]};
-            R fplus = recon(plus_in, lam, cf.weights, cf.eps, (ReconDetail*)nullptr);
-            R fminus = recon(minus_in, lam, cf.weights, cf.eps, (ReconDetail*)nullptr);
+            R fplus = recon(plus_in, lam, wrule, cf.eps, (ReconDetail*)nullptr);
+            R fminus = recon(minus_in, lam, wrule, cf.eps, (ReconDetail*)nullptr);
             /* Eq. reconstruction1 */
             R fs = fplus + fminus;
             /* Eq. reconstruction2 */
@@ -522,6 +529,10 @@ static void fill_ghosts_dir(Grid& G, int a, double t)
                             fixed = (x < xs) ? c.bc_state[0] : c.bc_state[1];
                         } else if (bc == BC_INFLOW) {
                             fixed = c.bc_state[0];
+                        } else if (bc == BC_JET) {
+                            double y = G.dim_eff > 1 ? G.center(1, dst[1]) : 0.0;
+                            kind = BC_INFLOW;
+                            fixed = (y < JET_HALF_WIDTH) ? c.bc_state[0] : c.bc_state[1];
                         }
                         if (kind == BC_INFLOW) {
                             for (int v = 0; v < nv; ++v)
@@ -646,12 +657,36 @@ static int state_ok(const Grid& G)
     return 1;
 }
 
-/* CFL rule: dt = CFL / max_cells sum_d (|u_d| + c) / dx_d */
+/* wave-speed sum of one conservative state (CFL rule) */
+static double state_speed(const Grid& G, const double* Uc)
+{
+    const or_cfg& c = G.c;
+    double s = 0.0;
+    for (int a = 0; a < G.dim_eff; ++a) {
+        CellQ<double> q;
+        cell_quantities(c, a, Uc, q);
+        if (c.dim == 0) s += std::fabs(c.adv_speed) / G.dx[a];
+        else s += (std::fabs(q.u[a]) + q.c) / G.dx[a];
+    }
+    return s;
+}
+
+/* CFL rule: dt = CFL / max sum_d (|u_d| + c) / dx_d over the interior cells
+ * and the fixed boundary states (they enter the domain through the ghost
+ * cells; copied ghosts repeat interior speeds) */
 static double cfl_dt(const Grid& G)
 {
     const or_cfg& c = G.c;
     if (c.dt_fixed > 0.0) return c.dt_fixed;
     double smax = 0.0;
+    for (int a = 0; a < G.dim_eff; ++a)
+        for (int side = 0; side < 2; ++side) {
+            const int bc = side == 0 ? c.bc_lo[a] : c.bc_hi[a];
+            const bool s0 = bc == BC_INFLOW || bc == BC_DMR_BOTTOM || bc == BC_DMR_TOP || bc == BC_JET;
+            const bool s1 = bc == BC_DMR_TOP || bc == BC_JET;
+            if (s0) smax = std::max(smax, state_speed(G, c.bc_state[0]));
+            if (s1) smax = std::max(smax, state_speed(G, c.bc_state[1]));
+        }
     for (int k = 0; k < G.n[2]; ++k)
         for (int j = 0; j < G.n[1]; ++j)
             for (int i = 0; i < G.n[0]; ++i) {
@@ -719,7 +754,7 @@ static void rhs_jvp_grid(const or_cfg& c, double t, const double* Ui, const doub
     for (int a = 0; a < G.dim_eff; ++a)
         for (int side = 0; side < 2; ++side) {
             const int bc = side == 0 ? c.bc_lo[a] : c.bc_hi[a];
-            if (bc != BC_INFLOW && bc != BC_DMR_BOTTOM && bc != BC_DMR_TOP) continue;
+            if (bc != BC_INFLOW && bc != BC_DMR_BOTTOM && bc != BC_DMR_TOP && bc != BC_JET) continue;
             int lim[3] = {G.n[0], G.n[1], G.n[2]};
             lim[a] = 1;
             for (int p2 = 0; p2 < lim[2]; ++p2)
@@ -728,7 +763,7 @@ static void rhs_jvp_grid(const or_cfg& c, double t, const double* Ui, const doub
                         for (int gl = 1; gl <= NG; ++gl) {
                             int ix[3] = {p0, p1, p2};
                             ix[a] = side == 0 ? -gl : G.n[a] - 1 + gl;
-                            bool fixed = bc == BC_INFLOW || bc == BC_DMR_TOP;
+                            bool fixed = bc == BC_INFLOW || bc == BC_DMR_TOP || bc == BC_JET;
                             if (bc == BC_DMR_BOTTOM) fixed = G.center(0, ix[0]) < 1.0 / 6.0;
                             if (fixed)
                                 for (int v = 0; v < G.nv; ++v) H.at(v, ix[0], ix[1], ix[2]) = 0.0;

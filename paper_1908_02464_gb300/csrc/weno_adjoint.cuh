@@ -577,7 +577,7 @@ __global__ void k_ghost_adj(GhostArgs a, const void* ghost_, void* G_)
             if (bc == BC_DMR_BOTTOM) {
                 const double x = a.lo0 + (i + 0.5) * a.dx0;
                 bc = x < 1.0 / 6.0 ? BC_INFLOW : BC_REFLECT;
-            } else if (bc == BC_DMR_TOP) {
+            } else if (bc == BC_DMR_TOP || bc == BC_JET) {
                 bc = BC_INFLOW;
             }
             if (bc == BC_INFLOW) continue;

@@ -52,6 +52,7 @@ struct weno_ctx {
     int tot_blocks = 1;
     int phase = 0;
     int tile[3] = {0, 0, 0};    // sweep tile variant per direction
+    double smax_floor = 0.0;    // CFL wave-speed sum of the fixed boundary states
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     bool graphs_ready = false;
     std::string err;
@@ -138,6 +139,8 @@ static wis::GhostArgs ghost_args(weno_ctx* c, void* U, int dir)
         for (int v = 0; v < 5; ++v) a.bc_state[s][v] = c->g.bc_state[s][v];
     a.lo0 = c->g.lo[0];
     a.dx0 = c->dx[0];
+    a.lo1 = c->g.lo[1];
+    a.dx1 = c->dx[1];
     return a;
 }
 
@@ -207,7 +210,7 @@ static cudaError_t issue_step(weno_ctx* c, int ph, cudaStream_t s)
     ca.tm = c->tm;
     cudaError_t e = do_cfl(c, ca, s);
     if (e != cudaSuccess) return e;
-    wis::k_dt<<<1, 1, 0, s>>>(c->tm, c->p.cfl);
+    wis::k_dt<<<1, 1, 0, s>>>(c->tm, c->p.cfl, c->smax_floor);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = issue_stage(c, cur, nullptr, x, 0.0, 1.0, 0.0, 0, s)) != cudaSuccess) return e;
     if ((e = issue_stage(c, x, cur, y, 0.75, 0.25, 1.0, 1, s)) != cudaSuccess) return e;
@@ -299,7 +302,8 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
         g_create_err = "unknown precision";
         return WENO_ERR_INVALID_ARG;
     }
-    if (params->weights < 0 || params->weights > 3 || params->splitting < 0 || params->splitting > 2) {
+    if (params->weights < 0 || params->weights > 3 || params->splitting < 0 || params->splitting > 2 ||
+        params->hybrid < 0 || params->hybrid > 2) {
         g_create_err = "unknown weights or splitting";
         return WENO_ERR_INVALID_ARG;
     }
@@ -312,7 +316,7 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
         if (!(grid->hi[d] > grid->lo[d])) { g_create_err = "hi must exceed lo"; return WENO_ERR_INVALID_ARG; }
         for (int s = 0; s < 2; ++s) {
             const int bc = s == 0 ? grid->bc_lo[d] : grid->bc_hi[d];
-            if (bc < WENO_BC_TRANSMISSIVE || bc > WENO_BC_DMR_TOP) {
+            if (bc < WENO_BC_TRANSMISSIVE || bc > WENO_BC_JET) {
                 g_create_err = "unknown boundary code";
                 return WENO_ERR_INVALID_ARG;
             }
@@ -345,6 +349,28 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
             ctx->eps_h[d] = eh;
         }
     }
+    // CFL: the fixed boundary states (inflow, double Mach, jet) enter through
+    // the ghost cells, so their wave speeds bound the time step as well
+    for (int d = 0; d < dim; ++d)
+        for (int side = 0; side < 2; ++side) {
+            const int bc = side == 0 ? grid->bc_lo[d] : grid->bc_hi[d];
+            const bool s0 = bc == WENO_BC_INFLOW || bc == WENO_BC_DMR_BOTTOM || bc == WENO_BC_DMR_TOP ||
+                            bc == WENO_BC_JET;
+            const bool s1 = bc == WENO_BC_DMR_TOP || bc == WENO_BC_JET;
+            for (int k = 0; k < 2; ++k) {
+                if (!(k == 0 ? s0 : s1)) continue;
+                const double* U = grid->bc_state[k];
+                const double rho = U[0];
+                double q2 = 0.0;
+                double u[3] = {0, 0, 0};
+                for (int e = 0; e < dim; ++e) { u[e] = U[1 + e] / rho; q2 += u[e] * u[e]; }
+                const double p = (params->gamma - 1.0) * (U[dim + 1] - 0.5 * rho * q2);
+                const double c = std::sqrt(params->gamma * p / rho);
+                double s = 0.0;
+                for (int e = 0; e < dim; ++e) s += (std::fabs(u[e]) + c) / ctx->dx[e];
+                if (s > ctx->smax_floor) ctx->smax_floor = s;
+            }
+        }
     // x: interior starts at element 32 so that rows of the interior are aligned
     const int xoff = 32;
     ctx->N[0] = ((xoff + ctx->n[0] + 3 + 31) / 32) * 32;
@@ -531,8 +557,9 @@ weno_status weno_face_flags(weno_ctx* ctx, const void* U_dev, double t, uint8_t*
 weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, void* gU_dev, double t)
 {
     if (!ctx || !U_dev || !w_dev || !gU_dev) return WENO_ERR_INVALID_ARG;
-    if (ctx->p.weights != 0 || ctx->p.splitting != wis::SPLIT_LLF) {
-        ctx->err = "the adjoint is implemented for the regularized weights with LLF splitting";
+    if (ctx->p.weights != 0 || ctx->p.splitting != wis::SPLIT_LLF || ctx->p.hybrid == 2) {
+        ctx->err = "the adjoint is implemented for the regularized weights with LLF splitting and the "
+                   "per-face hybrid switch";
         return WENO_ERR_UNSUPPORTED;
     }
     weno_status st = ensure_rhs_bufs(ctx);

@@ -78,7 +78,8 @@ struct FaceRec {
     static constexpr int AM = LAM + NV;       // alpha^{u-c}
     static constexpr int A0 = AM + 1;         // alpha^{u}, shear
     static constexpr int AP = AM + 2;         // alpha^{u+c}
-    static constexpr int NR = AM + 3;
+    static constexpr int MASK = AM + 3;       // per-field smooth bits (per-field hybrid)
+    static constexpr int NR = AM + 4;
 };
 
 // WENO faces are processed in chunks of QC queued faces.
@@ -221,9 +222,10 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             T w[NV];
             proj_all<T, DIM, DIR>(r, dU, w);
             const T lim = lim0 * (r.rt * r.rt);
-            bool smooth = a.hybrid != 0;
+            int fmask = 0;
 #pragma unroll
-            for (int s = 0; s < NV; ++s) smooth = smooth && lt_nn(w[s] * w[s], lim);
+            for (int s = 0; s < NV; ++s) fmask |= lt_nn(w[s] * w[s], lim) ? (1 << s) : 0;
+            const bool smooth = a.hybrid != 0 && fmask == (1 << NV) - 1;
             // splitting speeds: LLF max over the six stencil cells, global
             // LF maxima, or the Roe-average eigenvalues
             T am, a0, ap;
@@ -281,6 +283,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
                 fr[FR::AM * NFACE + f] = am;
                 fr[FR::A0 * NFACE + f] = a0;
                 fr[FR::AP * NFACE + f] = ap;
+                fr[FR::MASK * NFACE + f] = T(a.hybrid == 2 ? fmask : 0);
             }
             // a face is owned by the tile left of it, the last face by the last tile
             const int face = c0 + p;
@@ -357,10 +360,13 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             const int s = rem >> 1, sg = rem & 1;
             const int f = queue[q0 + q];
             const T lam = fr[(FR::LAM + s) * NFACE + f];
+            // per-field hybrid: the linear scheme for a smooth field
+            const int fm_bits = (int)fr[FR::MASK * NFACE + f];
+            const int wm = (fm_bits >> s) & 1 ? W_LINEAR : a.wmode;
             const T* v = fpm + ((q * NV + s) * 2 + sg) * 6;
             T out;
-            if (sg == 0) out = recon<T>(v[0], v[1], v[2], v[3], v[4], lam, eps, a.wmode);
-            else out = recon<T>(v[5], v[4], v[3], v[2], v[1], lam, eps, a.wmode);
+            if (sg == 0) out = recon<T>(v[0], v[1], v[2], v[3], v[4], lam, eps, wm);
+            else out = recon<T>(v[5], v[4], v[3], v[2], v[1], lam, eps, wm);
             res[(q * NV + s) * 2 + sg] = out;
         }
         __syncthreads();
@@ -466,12 +472,16 @@ struct GhostArgs {
     int bc_lo, bc_hi;
     double bc_state[2][5];
     double lo0, dx0;     // x-axis geometry for the DMR boundaries
+    double lo1, dx1;     // y-axis geometry for the jet inflow
     DevTime* tm;         // stage time from tm (t + stage_c dt), or t_fixed
     double stage_c, t_fixed;
 };
 
 enum { BC_TRANSMISSIVE = 0, BC_REFLECT = 1, BC_PERIODIC = 2, BC_INFLOW = 3, BC_DMR_BOTTOM = 4,
-       BC_DMR_TOP = 5 };
+       BC_DMR_TOP = 5, BC_JET = 6 };
+
+// half width of the inflow jet (bc_state[0] where y < JET_HALF_WIDTH)
+constexpr double JET_HALF_WIDTH = 0.05;
 
 template <typename T, int DIM>
 __global__ void k_ghost(GhostArgs a)
@@ -517,6 +527,10 @@ __global__ void k_ghost(GhostArgs a)
             bc = BC_INFLOW;
         } else if (bc == BC_INFLOW) {
             fixed = a.bc_state[0];
+        } else if (bc == BC_JET) {
+            const double y = a.lo1 + (j + 0.5) * a.dx1;
+            fixed = (y < JET_HALF_WIDTH) ? a.bc_state[0] : a.bc_state[1];
+            bc = BC_INFLOW;
         }
         const long long gdst = base + (long long)dst * sd;
         if (bc == BC_INFLOW) {
@@ -672,13 +686,15 @@ __global__ void __launch_bounds__(256) k_lf_alpha(CflArgs a, unsigned long long*
 }
 
 // dt = CFL / smax clipped to t_end; resets the reduction cell
-static __global__ void k_dt(DevTime* tm, double cfl)
+// smax_floor: wave-speed sum of the fixed boundary states (they enter the
+// domain through the ghost cells)
+static __global__ void k_dt(DevTime* tm, double cfl, double smax_floor)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double dt = 0.0;
     int clipped = 0;
     if (tm->status == 0) {
-        const double smax = __longlong_as_double((long long)tm->smax_bits);
+        const double smax = maxT(__longlong_as_double((long long)tm->smax_bits), smax_floor);
         dt = cfl_step(cfl, smax, tm->t, tm->t_end, &clipped);
     }
     tm->dt = dt;

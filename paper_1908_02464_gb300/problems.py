@@ -21,7 +21,7 @@ import math
 
 import numpy as np
 
-BC_TRANSMISSIVE, BC_REFLECT, BC_PERIODIC, BC_INFLOW, BC_DMR_BOTTOM, BC_DMR_TOP = range(6)
+BC_TRANSMISSIVE, BC_REFLECT, BC_PERIODIC, BC_INFLOW, BC_DMR_BOTTOM, BC_DMR_TOP, BC_JET = range(7)
 
 
 def centers(lo: float, hi: float, n: int) -> np.ndarray:
@@ -144,6 +144,25 @@ def double_mach(nx: int = 2048, ny: int = 512):
                  [BC_TRANSMISSIVE, BC_DMR_TOP], 0.2, "double_mach",
                  bc_state=[list(map(float, Upost)) + [0.0], list(map(float, Upre)) + [0.0]])
     return prob, prim_to_cons(gamma, rho, [u, v], p)
+
+
+def mach2000_jet(nx: int = 640, ny: int = 160):
+    """Mach 2000 jet of Sec. 4.7 on [0,1] x [0,0.25], gamma = 5/3, CFL 0.25,
+    t = 0.001.  Ambient (rho, u, v, p) = (0.5, 0, 0, 0.4127); the left
+    boundary injects (5, 800, 0, 0.4127) where y < 0.05 and the ambient state
+    elsewhere; reflecting bottom, outflow right and top."""
+    gamma = 5.0 / 3.0
+    amb = (0.5, 0.0, 0.0, 0.4127)
+    jet = (5.0, 800.0, 0.0, 0.4127)
+    shape = (ny, nx)
+
+    def cons(s):
+        return prim_to_cons(gamma, np.array(s[0]), [np.array(s[1]), np.array(s[2])], np.array(s[3]))
+    prob = _base(2, [nx, ny], [0.0, 0.0], [1.0, 0.25], [BC_JET, BC_REFLECT], [BC_TRANSMISSIVE, BC_TRANSMISSIVE],
+                 0.001, "mach2000_jet", gamma=gamma, cfl=0.25,
+                 bc_state=[list(map(float, cons(jet))) + [0.0], list(map(float, cons(amb))) + [0.0]])
+    U = prim_to_cons(gamma, np.full(shape, amb[0]), [np.zeros(shape), np.zeros(shape)], np.full(shape, amb[3]))
+    return prob, U
 
 
 def vortex3d(n: int = 256):

@@ -139,6 +139,42 @@ def test_full_run_parity_variants(case):
     assert np.mean(np.abs(V[0] - Uo[0])) <= 1e-10
 
 
+@pytest.mark.parametrize("dim,n", [(1, [201]), (2, [70, 23]), (3, [21, 14, 9])])
+def test_rhs_parity_per_field_hybrid(dim, n):
+    prob, U = P.random_state(dim, n, seed=81 + dim, kind="mixed")
+    prob["hybrid"] = 2
+    _compare_rhs(prob, U)
+
+
+def test_full_run_parity_per_field_hybrid():
+    prob, U = P.shu_osher(400)
+    prob["hybrid"] = 2
+    prob["t_end"] = 0.9
+    Uo = U.copy()
+    st, to, ko = orc.advance(prob, Uo, 0.0, prob["t_end"])
+    V, t, k = _run_gpu(prob, U)
+    assert st == 0 and t == to and k == ko
+    assert np.mean(np.abs(V[0] - Uo[0])) <= 1e-10
+
+
+def test_mach2000_jet_parity_first_steps():
+    """Sec. 4.7 jet (inflow-jet boundary, gamma 5/3, CFL 0.25): the first 30
+    steps against the oracle.  Both stop later with a negative pressure (the
+    scheme has no positivity limiter)."""
+    prob, U = P.mach2000_jet(160, 40)
+    Uo = U.copy()
+    st, to, ko = orc.advance(prob, Uo, 0.0, prob["t_end"], max_steps=30)
+    assert st == 0 and ko == 30
+    s = weno.Solver(prob, "fp64")
+    s.set_state(U)
+    k = s.advance(prob["t_end"], max_steps=30)
+    V, t = s.get_state()
+    s.close()
+    assert k == 30 and t == pytest.approx(to, rel=1e-13)
+    assert np.mean(np.abs(V[0] - Uo[0])) <= 1e-10 * np.mean(np.abs(Uo[0]))
+    _compare_rhs(prob, Uo, t=to)
+
+
 def test_rhs_parity_boundaries():
     """Shock tubes (transmissive), blast waves with reflecting walls (LLF on
     the GPU path), double Mach reflection (inflow, DMR bottom/top at t>0)."""

@@ -535,3 +535,35 @@ def test_rhs_jvp_is_linear_in_the_tangent():
     _, b = orc.rhs_jvp(prob, U, V2)
     _, c = orc.rhs_jvp(prob, U, 2.0 * V1 - 3.0 * V2)
     assert np.allclose(c, 2.0 * a - 3.0 * b, rtol=1e-9, atol=1e-9 * np.max(np.abs(c)))
+
+
+def test_cfl_step_covers_fixed_boundary_states():
+    """The inflow jet's boundary state (u = 800) enters through the ghost
+    cells, so it bounds the first time step although the interior is still."""
+    prob, U = P.mach2000_jet(64, 16)
+    g = prob["gamma"]
+    dx, dy = 1.0 / 64, 0.25 / 16
+
+    def speed(rho, u, v, p):
+        c = math.sqrt(g * p / rho)
+        return (abs(u) + c) / dx + (abs(v) + c) / dy
+    smax = max(speed(5.0, 800.0, 0.0, 0.4127), speed(0.5, 0.0, 0.0, 0.4127))
+    assert orc.cfl_dt(prob, U) == pytest.approx(prob["cfl"] / smax, rel=1e-14)
+    # problems without fixed states keep the interior rule
+    prob, U = P.sod(50)
+    rho, u, p = U[0], U[1] / U[0], 0.4 * (U[2] - 0.5 * U[1] ** 2 / U[0])
+    ref = 0.5 / np.max((np.abs(u) + np.sqrt(1.4 * p / rho)) * 50)
+    assert orc.cfl_dt(prob, U) == pytest.approx(ref, rel=1e-14)
+
+
+def test_per_field_hybrid_uses_linear_weights_only_on_smooth_fields():
+    """hybrid = 2: on a non-smooth face each field with sigma^s < eps_h takes
+    the optimal linear weights; with every field non-smooth it equals the
+    per-face switch, and it never changes smooth faces."""
+    prob, U = P.random_state(2, [40, 24], seed=17, kind="mixed")
+    r1, f1, ratio = orc.rhs(prob, U, 0.0, want_flags=True)
+    p2 = dict(prob, hybrid=2)
+    r2, f2, _ = orc.rhs(p2, U, 0.0, want_flags=True)
+    assert np.array_equal(f1, f2)
+    assert not np.array_equal(r1, r2)   # some WENO face has a smooth field
+    assert np.max(np.abs(r2 - r1)) < 0.1 * np.max(np.abs(r1))
