@@ -194,14 +194,15 @@ weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t fl
                              unsigned long long* weno_faces);
 
 /* Tile autotuner (no counterpart in the paper): for every sweep direction,
- * times each compiled tile shape (lines x cells per CTA: 2x63, 8x15, 4x31)
+ * times each compiled tile shape (lines x cells per CTA: 2x63, 8x15, 4x31,
+ * 1x127, 1x95)
  * `reps` times on the current state and keeps the fastest for this
  * context; variants[3] (if not NULL) receives the choice per direction.
  * The state is not changed; the step graphs are rebuilt on next use.
  * Synchronizes. */
 weno_status weno_autotune(weno_ctx* ctx, int reps, int* variants);
 
-/* Pin the tile shape of every sweep direction (variants[d] in 0..2, see
+/* Pin the tile shape of every sweep direction (variants[d] in 0..4, see
  * weno_autotune; ignored in 1D).  Results do not depend on the tile shape:
  * every face is computed by the same arithmetic.  WENO_ERR_INVALID_ARG for
  * an unknown variant. */

@@ -410,9 +410,11 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
         return WENO_ERR_CUDA;
     }
     std::memset(ctx->tm_host, 0, sizeof(DevTime));
-    // default tiles: long tiles in FP64 (ALU bound); coalesced rows for the
-    // float y/z sweeps
-    for (int d = 1; d < dim; ++d) ctx->tile[d] = ctx->prec == WENO_FP64 ? 0 : 1;
+    // default tiles (measured on GB300): single long lines in FP64 (ALU
+    // bound, least halo work); coalesced 8-column rows for the float y/z
+    // sweeps
+    for (int d = 0; d < dim; ++d) ctx->tile[d] = (ctx->prec == WENO_FP64 || d == 0) ? 3 : 1;
+    if (dim == 1) ctx->tile[0] = 0;
     *out = ctx;
     return WENO_OK;
 }

@@ -20,11 +20,15 @@ namespace wis {
 //   2 medium 4 x 31
 // FP64 is ALU bound (variant 0 everywhere); FP32 y/z sweeps prefer coalesced
 // rows.  weno_autotune times the variants on a live state and keeps the best.
-constexpr int kTileVariants = 3;
+//   3 single  1 x 127 halo work ~5%
+//   4 small   1 x 95  96-thread CTAs (more resident CTAs per SM)
+constexpr int kTileVariants = 5;
 template <int V> struct Tile;
 template <> struct Tile<0> { static constexpr int LINES = 2, SEG = 63, NT = 128; };
 template <> struct Tile<1> { static constexpr int LINES = 8, SEG = 15, NT = 128; };
 template <> struct Tile<2> { static constexpr int LINES = 4, SEG = 31, NT = 128; };
+template <> struct Tile<3> { static constexpr int LINES = 1, SEG = 127, NT = 128; };
+template <> struct Tile<4> { static constexpr int LINES = 1, SEG = 95, NT = 96; };
 struct Tile1D { static constexpr int LINES = 1, SEG = 127, NT = 128; };
 
 template <typename T, int DIM, int DIR, bool EXACTDET, typename TL>
@@ -55,6 +59,8 @@ cudaError_t launch_sweep_v(int variant, const SweepArgs& a, cudaStream_t s)
 {
     if (variant == 1) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<1>>(a, s);
     if (variant == 2) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<2>>(a, s);
+    if (variant == 3) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<3>>(a, s);
+    if (variant == 4) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<4>>(a, s);
     return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<0>>(a, s);
 }
 
