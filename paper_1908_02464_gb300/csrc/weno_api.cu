@@ -109,7 +109,7 @@ static wis::SweepArgs sweep_args(weno_ctx* c, int dir)
     a.wmode = c->p.weights;
     a.split = c->p.splitting;
     a.weno_count = c->wcount;
-    a.inv_dx_f = (float)a.inv_dx;
+    a.inv_dx_f = (float)(a.inv_dx * (1.0 / 60.0));   // face fluxes are kept times 60
     a.gamma_f = (float)a.gamma;
     a.eps_f = (float)a.eps;
     a.lim0_f = (float)(3600.0 * a.eps_h);

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs b)
         a.eps_h = eps_h;
         a.gamma = b.gamma; a.eps = b.eps; a.c_lambda = b.c_lambda; a.hybrid = b.hybrid;
         a.wmode = b.wmode; a.split = b.split; a.alpha_g = nullptr;
-        a.inv_dx_f = (float)a.inv_dx; a.gamma_f = (float)b.gamma; a.eps_f = (float)b.eps;
+        a.inv_dx_f = (float)(a.inv_dx * (1.0 / 60.0)); a.gamma_f = (float)b.gamma; a.eps_f = (float)b.eps;
         a.lim0_f = (float)(3600.0 * eps_h); a.lam_scale_f = (float)(b.c_lambda * (1.0 / 3600.0));
         const T inv_dx_t[1] = {T(a.inv_dx)};
         const int ntiles = (n + SEG - 1) / SEG;

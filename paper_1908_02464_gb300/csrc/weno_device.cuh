@@ -83,7 +83,8 @@ __device__ __forceinline__ void cell_prepare(const T* U, T gamma, T* q)
     for (int k = 0; k < DIM; ++k) m2 = fmaT(U[1 + k], U[1 + k], m2);
     const T E = U[DIM + 1];
     const T p = gm1 * fmaT(T(-0.5) * irho, m2, E);
-    const T c = Ar<T>::sqrt_(gamma * p * irho);
+    const T c2 = gamma * p * irho;
+    const T c = c2 * Ar<T>::rsqrt_(c2);   // sqrt(c2) without the correctly rounded sqrt sequence
     const T un = U[1 + DIR] * irho;
     const T Ep = E + p;
 #pragma unroll

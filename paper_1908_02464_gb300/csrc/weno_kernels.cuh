@@ -265,8 +265,9 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
                 for (int s = 1; s < NV - 1; ++s) aw[s] = a0 * w[s];
                 aw[NV - 1] = ap * w[NV - 1];
                 back_proj_add<T, DIM, DIR>(r, aw, Fo);
+                // face fluxes are kept times 60; the divergence scales by dx/60
 #pragma unroll
-                for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = Fo[v] * T(1.0 / 60.0);
+                for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = Fo[v];
             } else {
                 weno = true;
 #pragma unroll
@@ -387,7 +388,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             }
             back_proj_add<T, DIM, DIR>(r, wch, Fo);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = Fo[v];
+            for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = T(60) * Fo[v];
         }
     }
     __syncthreads();
@@ -395,7 +396,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
         atomicAdd(a.weno_count, (unsigned long long)wcount);
 
     // ---- flux divergence and output ---------------------------------------
-    const T inv_dx = pick<T>(a.inv_dx, a.inv_dx_f);
+    const T inv_dx = pick<T>(a.inv_dx * (1.0 / 60.0), a.inv_dx_f);
     T* outp = reinterpret_cast<T*>(a.out);
     T* accp = reinterpret_cast<T*>(a.acc);
     const T* Unp = reinterpret_cast<const T*>(a.Un);
