@@ -54,7 +54,10 @@ typedef enum {
                         hybrid switch (Eq. eq27-28, eq31) in double             */
 } weno_precision;
 
-/* boundary codes, one per side and direction (ghost cells, three layers) */
+/* boundary codes, one per side and direction (ghost cells, three layers).
+   The double Mach codes are accepted only on the y boundaries and the jet
+   only on the x boundaries of a 2D or 3D grid (weno_create returns
+   WENO_ERR_INVALID_ARG otherwise). */
 enum {
     WENO_BC_TRANSMISSIVE = 0, /* copy of the nearest interior cell                    */
     WENO_BC_REFLECT = 1,      /* mirror image, normal momentum negated                */

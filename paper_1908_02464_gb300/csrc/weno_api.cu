@@ -114,6 +114,17 @@ static wis::SweepArgs sweep_args(weno_ctx* c, int dir)
     a.eps_f = (float)a.eps;
     a.lim0_f = (float)(3600.0 * a.eps_h);
     a.lam_scale_f = (float)(a.c_lambda * (1.0 / 3600.0));
+    a.bc_lo = c->g.bc_lo[dir];
+    a.bc_hi = c->g.bc_hi[dir];
+    for (int s = 0; s < 2; ++s)
+        for (int v = 0; v < 5; ++v) {
+            a.bc_state[s][v] = c->g.bc_state[s][v];
+            a.bc_state_f[s][v] = (float)c->g.bc_state[s][v];
+        }
+    a.lo0 = c->g.lo[0];
+    a.dx0 = c->dx[0];
+    a.lo1 = c->g.lo[1];
+    a.dx1 = c->dx[1];
     return a;
 }
 
@@ -160,7 +171,8 @@ static cudaError_t issue_lf(weno_ctx* c, const void* in, int slot, DevTime* tm, 
     return c->prec == WENO_FP64 ? wis::lf_f64(c->dim, ca, out, c->nsm, s) : wis::lf_f32(c->dim, ca, out, c->nsm, s);
 }
 
-// one RK stage: ghosts of `in` at the stage time, then the sweeps
+// one RK stage: the sweeps of `in`, whose tiles take their ghost cells from
+// the boundary conditions at the stage time t + stage_c dt
 static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* out, double ra, double rb,
                                double stage_c, int slot, cudaStream_t s)
 {
@@ -169,16 +181,10 @@ static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* ou
         if (e != cudaSuccess) return e;
     }
     for (int d = 0; d < c->dim; ++d) {
-        wis::GhostArgs ga = ghost_args(c, in, d);
-        ga.tm = c->tm;
-        ga.stage_c = stage_c;
-        cudaError_t e = do_ghost(c, ga, s);
-        if (e != cudaSuccess) return e;
-    }
-    for (int d = 0; d < c->dim; ++d) {
         wis::SweepArgs a = sweep_args(c, d);
         a.U = in;
         a.tm = c->tm;
+        a.stage_c = stage_c;
         a.alpha_g = c->alpha_g + slot * 9 + 3 * d;
         if (d == c->dim - 1) {
             a.mode = wis::MODE_COMBINE;
@@ -318,6 +324,15 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
             const int bc = s == 0 ? grid->bc_lo[d] : grid->bc_hi[d];
             if (bc < WENO_BC_TRANSMISSIVE || bc > WENO_BC_JET) {
                 g_create_err = "unknown boundary code";
+                return WENO_ERR_INVALID_ARG;
+            }
+        }
+        for (int s = 0; s < 2; ++s) {
+            const int bc = s == 0 ? grid->bc_lo[d] : grid->bc_hi[d];
+            const bool dmr = bc == WENO_BC_DMR_BOTTOM || bc == WENO_BC_DMR_TOP;
+            if ((dmr && d != 1) || (bc == WENO_BC_JET && (d != 0 || dim < 2))) {
+                g_create_err = "double Mach boundaries belong on y boundaries, the jet on x boundaries of a "
+                               "multi-dimensional grid";
                 return WENO_ERR_INVALID_ARG;
             }
         }
@@ -504,19 +519,15 @@ static weno_status ensure_rhs_bufs(weno_ctx* ctx)
     return WENO_OK;
 }
 
-// ghosts + sweeps of a stand-alone RHS on rhs_in -> rhs_out (flags optional)
+// sweeps of a stand-alone RHS at time t on rhs_in -> rhs_out (flags optional)
 static weno_status issue_rhs(weno_ctx* ctx, double t, uint8_t* flags)
 {
-    for (int d = 0; d < ctx->dim; ++d) {
-        wis::GhostArgs ga = ghost_args(ctx, ctx->rhs_in, d);
-        ga.t_fixed = t;
-        CK(do_ghost(ctx, ga, ctx->stream));
-    }
     if (ctx->p.splitting == wis::SPLIT_LF) CK(issue_lf(ctx, ctx->rhs_in, 3, nullptr, ctx->stream));
     long long foff = 0;
     for (int d = 0; d < ctx->dim; ++d) {
         wis::SweepArgs a = sweep_args(ctx, d);
         a.U = ctx->rhs_in;
+        a.t_fixed = t;
         a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
         if (flags) a.flags = flags + foff;
         if (d == ctx->dim - 1) {
@@ -692,6 +703,7 @@ static weno_status time_sweep_dir(weno_ctx* ctx, int d, int reps, void* flush_de
         CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
         wis::SweepArgs a = sweep_args(ctx, d);
         a.U = cur;
+        a.t_fixed = ctx->tm_host->t;
         a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
         a.mode = wis::MODE_ACC_SET;
         a.acc = ctx->dim > 1 ? ctx->acc : ctx->rhs_out;
@@ -716,11 +728,6 @@ static weno_status prepare_timing(weno_ctx* ctx)
     if (st != WENO_OK) return st;
     if (ctx->dim == 1 && (st = ensure_rhs_bufs(ctx)) != WENO_OK) return st;
     void* cur = ctx->buf[ctx->phase];
-    for (int d = 0; d < ctx->dim; ++d) {
-        wis::GhostArgs ga = ghost_args(ctx, cur, d);
-        ga.t_fixed = ctx->tm_host->t;
-        CK(do_ghost(ctx, ga, ctx->stream));
-    }
     if (ctx->p.splitting == wis::SPLIT_LF) CK(issue_lf(ctx, cur, 3, nullptr, ctx->stream));
     return WENO_OK;
 }

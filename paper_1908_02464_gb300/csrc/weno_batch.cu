@@ -4,11 +4,12 @@
 //
 // Each CTA pulls an instance from a work queue (instances ordered largest
 // first, so the tail of the schedule holds the small ones), copies it into
-// three ghosted work arrays that stay L2-resident while it is being solved,
-// and runs the whole RK3 loop (Sec. 4 of the paper) with block-level
-// barriers only: CFL max-reduction, then per stage the ghost cells and a
-// chain of sweep tiles (the same per-tile code as the grid solver, so every
-// face is computed by identical arithmetic).  No CTA ever waits on another.
+// three work arrays that stay L2-resident while it is being solved, and runs
+// the whole RK3 loop (Sec. 4 of the paper) with block-level barriers only:
+// CFL max-reduction, then per stage a chain of sweep tiles (the same
+// per-tile code as the grid solver, which takes the ghost cells from the
+// boundary conditions while staging, so every face is computed by identical
+// arithmetic).  No CTA ever waits on another.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -53,27 +54,6 @@ template <> struct BatchTile<1> { static constexpr int SEG = 63, NT = 64; };
 template <> struct BatchTile<2> { static constexpr int SEG = 255, NT = 256; };
 constexpr int kBatchVariants = 3;
 
-template <typename T, int NT>
-__device__ __forceinline__ void batch_ghosts(T* W, int n, long long sv, int bc_lo, int bc_hi)
-{
-    // three ghost layers per side, 1D: transmissive, reflecting or periodic
-    if (threadIdx.x < 6) {
-        const int side = threadIdx.x / 3, gl = threadIdx.x % 3 + 1;
-        const int bc = side == 0 ? bc_lo : bc_hi;
-        const int dst = side == 0 ? -gl : n - 1 + gl;
-        int src;
-        if (bc == BC_TRANSMISSIVE) src = side == 0 ? 0 : n - 1;
-        else if (bc == BC_REFLECT) src = side == 0 ? gl - 1 : n - gl;
-        else src = side == 0 ? n - gl : gl - 1;
-#pragma unroll
-        for (int v = 0; v < 3; ++v) {
-            T val = W[3 + v * sv + src];
-            if (bc == BC_REFLECT && v == 1) val = -val;
-            W[3 + v * sv + dst] = val;
-        }
-    }
-}
-
 template <typename T, int SEG, int NT, bool EXACTDET>
 __global__ void __launch_bounds__(NT) k_batch(BatchArgs b)
 {
@@ -105,6 +85,8 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs b)
         for (int k = 0; k < b.alpha_thr; ++k) eps_h *= dx / b.L_char;
 
         SweepArgs a;
+        a.bc_lo = b.bc_lo;   // the tiles take their ghost cells from these
+        a.bc_hi = b.bc_hi;
         a.acc = nullptr;
         a.mode = MODE_COMBINE;
         a.tm = nullptr;
@@ -160,8 +142,6 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs b)
             const double ra[3] = {0.0, 0.75, 1.0 / 3.0}, rb[3] = {1.0, 0.25, 2.0 / 3.0};
             bool sbad = false;
             for (int st = 0; st < 3; ++st) {
-                batch_ghosts<T, NT>(W[in_[st]], n, sv, b.bc_lo, b.bc_hi);
-                __syncthreads();
                 a.U = W[in_[st]];
                 a.Un = W[cur];
                 a.out = W[out_[st]];

@@ -58,11 +58,74 @@ struct SweepArgs {
     // the same constants pre-rounded for float kernels (a double conversion
     // or division per thread would run on the slow FP64 pipe)
     float inv_dx_f, gamma_f, eps_f, lim0_f, lam_scale_f, rk_a_f, rk_b_f;
+    // boundary conditions of this direction, applied while staging the tile
+    // (the ghost cells are computed, not read)
+    int bc_lo, bc_hi;
+    double bc_state[2][5];
+    float bc_state_f[2][5];
+    double lo0, dx0, lo1, dx1;   // x and y geometry (double Mach, jet)
+    double stage_c, t_fixed;     // boundary time: tm->t + stage_c tm->dt, or t_fixed without tm
 };
 
 template <typename T> __device__ __forceinline__ T pick(double d, float f);
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+enum { BC_TRANSMISSIVE = 0, BC_REFLECT = 1, BC_PERIODIC = 2, BC_INFLOW = 3, BC_DMR_BOTTOM = 4,
+       BC_DMR_TOP = 5, BC_JET = 6 };
+
+// half width of the inflow jet (bc_state[0] where y < JET_HALF_WIDTH)
+constexpr double JET_HALF_WIDTH = 0.05;
+
+// State of cell `along` of a grid line (interior or one of the three ghost
+// cells per side), applying the boundary condition of direction DIR:
+// transmissive (nearest interior cell), reflecting (mirror, normal momentum
+// negated), periodic (wrap), fixed states (inflow, double Mach bottom and
+// top, jet).  `line` indexes the grid line: the row j for x sweeps, the
+// column i for y/z sweeps.
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void stage_cell(const SweepArgs& a, const T* Ug, long long line_base, int line, int along,
+                                           int nd, T* U)
+{
+    constexpr int NV = DIM + 2;
+    const long long sd = DIR == 0 ? 1LL : (DIR == 1 ? a.sy : a.sz);
+    int src = along;
+    bool flip = false;
+    if (along < 0 || along >= nd) {
+        const int side = along < 0 ? 0 : 1;
+        const int gl = side == 0 ? -along : along - nd + 1;
+        int bc = side == 0 ? a.bc_lo : a.bc_hi;
+        int fixed = -1;
+        if (bc == BC_INFLOW) {
+            fixed = 0;
+        } else if (bc == BC_DMR_BOTTOM) {
+            const double x = a.lo0 + (line + 0.5) * a.dx0;
+            if (x < 1.0 / 6.0) fixed = 0;
+            else bc = BC_REFLECT;
+        } else if (bc == BC_DMR_TOP) {
+            // shock position on the top boundary at the boundary time
+            const double t = a.tm != nullptr ? a.tm->t + a.stage_c * a.tm->dt : a.t_fixed;
+            const double xs = 1.0 / 6.0 + (1.0 + 20.0 * t) / sqrt(3.0);
+            const double x = a.lo0 + (line + 0.5) * a.dx0;
+            fixed = x < xs ? 0 : 1;
+        } else if (bc == BC_JET) {
+            const double y = a.lo1 + (line + 0.5) * a.dx1;
+            fixed = y < JET_HALF_WIDTH ? 0 : 1;
+        }
+        if (fixed >= 0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) U[v] = pick<T>(a.bc_state[fixed][v], a.bc_state_f[fixed][v]);
+            return;
+        }
+        if (bc == BC_TRANSMISSIVE) src = side == 0 ? 0 : nd - 1;
+        else if (bc == BC_REFLECT) { src = side == 0 ? gl - 1 : nd - gl; flip = true; }
+        else src = side == 0 ? nd - gl : gl - 1;
+    }
+    const long long g = line_base + (long long)src * sd;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) U[v] = Ug[g + v * a.sv];
+    if (flip) U[1 + DIR] = -U[1 + DIR];
+}
 
 template <typename T, int DIM>
 struct FaceRec {
@@ -157,21 +220,42 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
     if (threadIdx.x == 0) { qcount = 0; wcount = 0u; }
 
     // ---- stage the tile (cells c0-3 .. c0+SEG+2 of LINES lines) --------
-    for (int idx = threadIdx.x; idx < NCELL; idx += NT) {
-        int l, p;
-        if (DIR == 0) { l = idx / CELLS; p = idx - l * CELLS; }
-        else { p = idx / LINES; l = idx - p * LINES; }
-        const int line = line0 + l;
-        const int along = c0 - 3 + p;
-        if (line < nline && along < nd + 3) {
-            const long long g = a.off0 + (long long)line * sl + (long long)pb * sp + (long long)along * sd;
-            T U[NV];
+    auto put = [&](int idx, const T (&U)[NV]) {
+        T q[NQ];
+        cell_prepare<T, DIM, DIR>(U, gamma, q);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) U[v] = Ug[g + v * a.sv];
-            T q[NQ];
-            cell_prepare<T, DIM, DIR>(U, gamma, q);
+        for (int k = 0; k < NQ; ++k) cq[k * NCELL + idx] = q[k];
+    };
+    if (c0 >= 3 && c0 + SEG + 3 <= nd) {
+        // the whole halo is interior (uniform over the block)
+        for (int idx = threadIdx.x; idx < NCELL; idx += NT) {
+            int l, p;
+            if (DIR == 0) { l = idx / CELLS; p = idx - l * CELLS; }
+            else { p = idx / LINES; l = idx - p * LINES; }
+            const int line = line0 + l;
+            if (line < nline) {
+                const long long g =
+                    a.off0 + (long long)line * sl + (long long)pb * sp + (long long)(c0 - 3 + p) * sd;
+                T U[NV];
 #pragma unroll
-            for (int k = 0; k < NQ; ++k) cq[k * NCELL + idx] = q[k];
+                for (int v = 0; v < NV; ++v) U[v] = Ug[g + v * a.sv];
+                put(idx, U);
+            }
+        }
+    } else {
+        // a tile at an end of its lines: ghost cells from the boundary conditions
+        for (int idx = threadIdx.x; idx < NCELL; idx += NT) {
+            int l, p;
+            if (DIR == 0) { l = idx / CELLS; p = idx - l * CELLS; }
+            else { p = idx / LINES; l = idx - p * LINES; }
+            const int line = line0 + l;
+            const int along = c0 - 3 + p;
+            if (line < nline && along < nd + 3) {
+                T U[NV];
+                stage_cell<T, DIM, DIR>(a, Ug, a.off0 + (long long)line * sl + (long long)pb * sp, line, along,
+                                        nd, U);
+                put(idx, U);
+            }
         }
     }
     __syncthreads();
@@ -477,12 +561,6 @@ struct GhostArgs {
     DevTime* tm;         // stage time from tm (t + stage_c dt), or t_fixed
     double stage_c, t_fixed;
 };
-
-enum { BC_TRANSMISSIVE = 0, BC_REFLECT = 1, BC_PERIODIC = 2, BC_INFLOW = 3, BC_DMR_BOTTOM = 4,
-       BC_DMR_TOP = 5, BC_JET = 6 };
-
-// half width of the inflow jet (bc_state[0] where y < JET_HALF_WIDTH)
-constexpr double JET_HALF_WIDTH = 0.05;
 
 template <typename T, int DIM>
 __global__ void k_ghost(GhostArgs a)
