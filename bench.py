@@ -237,7 +237,9 @@ def run_ours(args) -> dict:
             Up, tp_ = sp.get_state()
             totp = sum(msp)
             d = np.abs(Up[0].astype(np.float64) - U64[0])
+            torch.cuda.nvtx.range_push(f"sweeps_{prec}")
             ms_d, wf_d = sp.time_sweeps(reps=5, flush=flush)
+            torch.cuda.nvtx.range_pop()
             dd = int(np.argmax(ms_d))
             flp = sweep_flops(2, [NX, NY], wf_d[dd], dd)
             peak32 = nsm * FP32_FLOP_PER_CLK_SM * sm_max * 1e6
@@ -274,8 +276,9 @@ def run_ours(args) -> dict:
 
     batch = None if args.no_batch else batched_riemann(args)
     vortex = None if args.no_vortex else vortex3d_rhs_vjp(args)
+    jet = None if args.no_jet else mach2000_jet_run(args)
 
-    launches_per_step = 3 + 3 * 2 * 2 + 1   # cfl, dt, post, 3 x (2 ghosts + 2 sweeps), set_tend
+    launches_per_step = 3 + 3 * 2 + 1   # cfl, dt, post, 3 stages x 2 sweeps, set_tend
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -292,6 +295,8 @@ def run_ours(args) -> dict:
         res["batched_riemann"] = batch
     if vortex is not None:
         res["vortex3d_256"] = vortex
+    if jet is not None:
+        res["mach2000_jet"] = jet
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
     if ws > 1:
@@ -338,6 +343,43 @@ def batched_riemann(args) -> dict:
             entry["l1_rho_vs_fp64_max"] = float(np.max(l1))
         out[prec] = entry
         b.close()
+    return out
+
+
+def mach2000_jet_run(args) -> dict:
+    """Mach 2000 jet of Sec. 4.7 at the paper's 640 x 160 to t = 0.001 (global
+    LF splitting, the workload's lambda reading), FP64 and mixed: whether the
+    run finishes, its steps and wall time, and the positivity margins."""
+    import torch
+    from paper_1908_02464_gb300 import problems as P
+    from paper_1908_02464_gb300 import weno
+    prob, U = P.mach2000_jet(640, 160)
+    out = {"grid": [640, 160], "t_end": prob["t_end"], "splitting": prob["splitting"],
+           "c_lambda": prob["c_lambda"]}
+    ref = None
+    for prec in ("fp64", "mixed"):
+        s = weno.Solver(prob, prec)
+        s.set_state(U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            k = s.advance(prob["t_end"])
+            status = "ok"
+        except weno.WenoError as e:
+            k, status = None, f"stopped: {e}"
+        wall = time.perf_counter() - t0
+        V, t = s.get_state()
+        s.close()
+        V = V.astype(np.float64)
+        g = prob["gamma"]
+        p = (g - 1.0) * (V[3] - 0.5 * (V[1] ** 2 + V[2] ** 2) / V[0])
+        entry = {"status": status, "steps": k, "t": t, "wall_s": wall, "rho_min": float(V[0].min()),
+                 "p_min": float(p.min())}
+        if prec == "fp64":
+            ref = V
+        elif status == "ok" and ref is not None:
+            entry["l1_rho_vs_fp64"] = float(np.mean(np.abs(V[0] - ref[0])))
+        out[prec] = entry
     return out
 
 
@@ -456,6 +498,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-vortex", action="store_true")
     ap.add_argument("--vortex-n", type=int, default=256)
+    ap.add_argument("--no-jet", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

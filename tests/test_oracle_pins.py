@@ -567,3 +567,25 @@ def test_per_field_hybrid_uses_linear_weights_only_on_smooth_fields():
     assert np.array_equal(f1, f2)
     assert not np.array_equal(r1, r2)   # some WENO face has a smooth field
     assert np.max(np.abs(r2 - r1)) < 0.1 * np.max(np.abs(r1))
+
+
+def test_mach2000_jet_runs_to_the_end_under_the_lambda_reading():
+    """Sec. 4.7 reports the method robust on the Mach 2000 jet without a
+    positivity limiter.  With global LF splitting and lambda formed from the
+    fifth difference without the 1/60 of Eq. eq28, the oracle reaches
+    t = 0.001 at 160 x 40 with positive density and pressure; with c = 1 on
+    the eq28 form it stops with a negative pressure early on."""
+    prob, U = P.mach2000_jet(160, 40)
+    U = np.ascontiguousarray(U)
+    st, t, k = orc.advance(prob, U, 0.0, prob["t_end"])
+    assert st == 0 and t == prob["t_end"] and k > 800
+    g = prob["gamma"]
+    p = (g - 1.0) * (U[3] - 0.5 * (U[1] ** 2 + U[2] ** 2) / U[0])
+    assert U[0].min() > 0.0 and p.min() > 0.0
+    # the jet has entered: the inflow density appears well inside the domain
+    assert U[0][:, 40:].max() > 5.0
+    prob, U = P.mach2000_jet(160, 40)
+    prob["c_lambda"] = 1.0
+    U = np.ascontiguousarray(U)
+    st, t, k = orc.advance(prob, U, 0.0, prob["t_end"])
+    assert st == 3 and k < 100   # non-physical state
