@@ -214,19 +214,30 @@ def run_ours(args) -> dict:
     peak64 = nsm * FP64_FLOP_PER_CLK_SM * sm_max * 1e6
     micro64, _ = weno.weno_measure_fma_peak(0)
     traffic = None
+    pipe_ncu = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         with open(tp) as f:
             tj = json.load(f)
         if tj.get("csrc_digest") == csrc_digest():
             traffic = tj.get("fp64", {}).get(f"sweep_dir{dom}")
+            pipe_ncu = tj.get("fp64", {}).get("pipe_fp64_pct_active", {}).get(f"sweep_dir{dom}")
+    hbm_peak = None
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        with open(mp) as f:
+            hbm_peak = json.load(f).get("hbm_gbs")
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak64, "traffic": traffic,
                 "kernel": f"k_sweep<double,2,{dom}> ({'x' if dom == 0 else 'y'}-sweep)",
                 "kernel_ms": ms_dir[dom], "alg_flops_per_launch": fl, "weno_faces_per_launch": int(wf_dir[dom]),
                 "peak_source": f"derived: {nsm} SMs x {FP64_FLOP_PER_CLK_SM} FP64 flop/clk x {sm_max:.0f} MHz",
                 "peak_fma_microbenchmark": micro64 / 1e12, "sweep_ms_per_dir": ms_dir,
-                "sweep_share_of_step": 3 * sum(ms_dir) / (tot / args.steps)}
+                "sweep_share_of_step": 3 * sum(ms_dir) / (tot / args.steps),
+                "fp64_pipe_pct_active_ncu": pipe_ncu,
+                "dram_gbs": None if traffic is None else traffic / (ms_dir[dom] * 1e-3) / 1e9,
+                "dram_frac_of_measured_hbm": (None if traffic is None or not hbm_peak
+                                              else traffic / (ms_dir[dom] * 1e-3) / 1e9 / hbm_peak)}
 
     # reduced-precision paths on the same state
     extra = {}
