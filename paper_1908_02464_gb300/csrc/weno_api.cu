@@ -172,9 +172,9 @@ static cudaError_t issue_lf(weno_ctx* c, const void* in, int slot, DevTime* tm, 
 }
 
 // one RK stage: the sweeps of `in`, whose tiles take their ghost cells from
-// the boundary conditions at the stage time t + stage_c dt
+// the boundary conditions at the time of stage `stage` (t, t + dt, t + dt/2)
 static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* out, double ra, double rb,
-                               double stage_c, int slot, cudaStream_t s)
+                               int stage, int slot, cudaStream_t s)
 {
     if (c->p.splitting == wis::SPLIT_LF) {
         cudaError_t e = issue_lf(c, in, slot, c->tm, s);
@@ -184,7 +184,7 @@ static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* ou
         wis::SweepArgs a = sweep_args(c, d);
         a.U = in;
         a.tm = c->tm;
-        a.stage_c = stage_c;
+        a.stage = stage;
         a.alpha_g = c->alpha_g + slot * 9 + 3 * d;
         if (d == c->dim - 1) {
             a.mode = wis::MODE_COMBINE;
@@ -218,9 +218,9 @@ static cudaError_t issue_step(weno_ctx* c, int ph, cudaStream_t s)
     if (e != cudaSuccess) return e;
     wis::k_dt<<<1, 1, 0, s>>>(c->tm, c->p.cfl, c->smax_floor);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = issue_stage(c, cur, nullptr, x, 0.0, 1.0, 0.0, 0, s)) != cudaSuccess) return e;
-    if ((e = issue_stage(c, x, cur, y, 0.75, 0.25, 1.0, 1, s)) != cudaSuccess) return e;
-    if ((e = issue_stage(c, y, cur, x, 1.0 / 3.0, 2.0 / 3.0, 0.5, 2, s)) != cudaSuccess) return e;
+    if ((e = issue_stage(c, cur, nullptr, x, 0.0, 1.0, 0, 0, s)) != cudaSuccess) return e;
+    if ((e = issue_stage(c, x, cur, y, 0.75, 0.25, 1, 1, s)) != cudaSuccess) return e;
+    if ((e = issue_stage(c, y, cur, x, 1.0 / 3.0, 2.0 / 3.0, 2, 2, s)) != cudaSuccess) return e;
     wis::k_post<<<1, 1, 0, s>>>(c->tm);
     return cudaGetLastError();
 }
@@ -527,7 +527,7 @@ static weno_status issue_rhs(weno_ctx* ctx, double t, uint8_t* flags)
     for (int d = 0; d < ctx->dim; ++d) {
         wis::SweepArgs a = sweep_args(ctx, d);
         a.U = ctx->rhs_in;
-        a.t_fixed = t;
+        a.xs_fixed = wis::dmr_shock_x(t);
         a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
         if (flags) a.flags = flags + foff;
         if (d == ctx->dim - 1) {
@@ -703,7 +703,7 @@ static weno_status time_sweep_dir(weno_ctx* ctx, int d, int reps, void* flush_de
         CK(cudaMemsetAsync(ctx->wcount, 0, sizeof(unsigned long long), ctx->stream));
         wis::SweepArgs a = sweep_args(ctx, d);
         a.U = cur;
-        a.t_fixed = ctx->tm_host->t;
+        a.xs_fixed = wis::dmr_shock_x(ctx->tm_host->t);
         a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
         a.mode = wis::MODE_ACC_SET;
         a.acc = ctx->dim > 1 ? ctx->acc : ctx->rhs_out;

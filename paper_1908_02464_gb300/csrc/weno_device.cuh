@@ -38,13 +38,30 @@ __device__ __forceinline__ float absT(float a) { return fabsf(a); }
 
 template <typename T> struct Ar;
 
+// Reciprocal refined by Newton's method from the hardware's approximate value
+// (rcp.approx): x <- x (2 - d x) squares the relative error of the estimate
+// at each step, so two steps reach double precision up to the rounding of
+// the last one.  For the finite, positive, normal arguments of the sweeps
+// (sums of square roots of densities, weight denominators).
+__device__ __forceinline__ double rcp_newton(double d)
+{
+    double x;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
+    double e = __fma_rn(-d, x, 1.0);   // 1 - d x
+    x = __fma_rn(x, e, x);             // x + x (1 - d x)
+    e = __fma_rn(-d, x, 1.0);
+    return __fma_rn(x, e, x);
+}
+
 template <> struct Ar<double> {
+    static __device__ __forceinline__ double rcp_f(double x) { return rcp_newton(x); }
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 };
 
 template <> struct Ar<float> {
+    static __device__ __forceinline__ float rcp_f(float x) { return __fdividef(1.0f, x); }
     static __device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
@@ -120,7 +137,7 @@ __device__ __forceinline__ Roe<T, DIM> roe_state(GA get_a, GB get_b, T gamma)
     using CL = CellLayout<DIM>;
     Roe<T, DIM> r;
     const T sa = get_a(CL::SQ), sb = get_b(CL::SQ);
-    const T inv = Ar<T>::rcp(sa + sb);
+    const T inv = Ar<T>::rcp_f(sa + sb);
     T q2 = T(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
@@ -267,7 +284,7 @@ __device__ __forceinline__ double recon<double>(double a, double b, double c, do
     const double w3 = 0.1 * (D3 + L23) * (D01 * D2);
     const double num = fmaT(w0, q0, fmaT(w1, q1, fmaT(w2, q2, w3 * q3)));
     const double den = (w0 + w1) + (w2 + w3);
-    return num / den;
+    return num * rcp_newton(den);
 }
 
 template <>

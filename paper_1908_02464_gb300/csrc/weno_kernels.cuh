@@ -31,7 +31,13 @@ struct DevTime {
     long long steps;                // completed steps
     int status;                     // 0 ok, else WENO_ERR_NONPHYSICAL latched
     int clipped;                    // 1 if dt was clipped to reach t_end
+    double xs_top[3];               // double Mach top boundary: shock position at the
+                                    // stage times t, t + dt, t + dt/2
 };
+
+// Shock position on the top boundary of the double Mach reflection at time t
+// (the Mach 10 shock through (1/6, 0) at 60 degrees moves at 10 / sin 60).
+__host__ __device__ inline double dmr_shock_x(double t) { return 1.0 / 6.0 + (1.0 + 20.0 * t) / sqrt(3.0); }
 
 enum { MODE_ACC_SET = 0, MODE_ACC_ADD = 1, MODE_COMBINE = 2, MODE_RHS = 3 };
 // flux splitting (Eq. flxuspliting): local LF over the six stencil cells,
@@ -64,7 +70,8 @@ struct SweepArgs {
     double bc_state[2][5];
     float bc_state_f[2][5];
     double lo0, dx0, lo1, dx1;   // x and y geometry (double Mach, jet)
-    double stage_c, t_fixed;     // boundary time: tm->t + stage_c tm->dt, or t_fixed without tm
+    int stage;                   // RK stage (index of tm->xs_top)
+    double xs_fixed;             // double Mach shock position when tm is null
 };
 
 template <typename T> __device__ __forceinline__ T pick(double d, float f);
@@ -104,8 +111,7 @@ __device__ __forceinline__ void stage_cell(const SweepArgs& a, const T* Ug, long
             else bc = BC_REFLECT;
         } else if (bc == BC_DMR_TOP) {
             // shock position on the top boundary at the boundary time
-            const double t = a.tm != nullptr ? a.tm->t + a.stage_c * a.tm->dt : a.t_fixed;
-            const double xs = 1.0 / 6.0 + (1.0 + 20.0 * t) / sqrt(3.0);
+            const double xs = a.tm != nullptr ? a.tm->xs_top[a.stage] : a.xs_fixed;
             const double x = a.lo0 + (line + 0.5) * a.dx0;
             fixed = x < xs ? 0 : 1;
         } else if (bc == BC_JET) {
@@ -601,7 +607,7 @@ __global__ void k_ghost(GhostArgs a)
             else bc = BC_REFLECT;
         } else if (bc == BC_DMR_TOP) {
             const double x = a.lo0 + (i + 0.5) * a.dx0;
-            const double xs = 1.0 / 6.0 + (1.0 + 20.0 * t) / sqrt(3.0);
+            const double xs = dmr_shock_x(t);
             fixed = (x < xs) ? a.bc_state[0] : a.bc_state[1];
             bc = BC_INFLOW;
         } else if (bc == BC_INFLOW) {
@@ -779,6 +785,10 @@ static __global__ void k_dt(DevTime* tm, double cfl, double smax_floor)
     tm->dt = dt;
     tm->clipped = clipped;
     tm->smax_bits = 0ull;
+    // boundary times of the three stages (Shu-Osher RK3: t, t + dt, t + dt/2)
+    tm->xs_top[0] = dmr_shock_x(tm->t);
+    tm->xs_top[1] = dmr_shock_x(tm->t + dt);
+    tm->xs_top[2] = dmr_shock_x(tm->t + 0.5 * dt);
 }
 
 // target time for the steps that follow on the stream
