@@ -197,15 +197,18 @@ weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t fl
                              unsigned long long* weno_faces);
 
 /* Tile autotuner (no counterpart in the paper): for every sweep direction,
- * times each compiled tile shape (lines x cells per CTA: 2x63, 8x15, 4x31,
- * 1x127, 1x95)
- * `reps` times on the current state and keeps the fastest for this
- * context; variants[3] (if not NULL) receives the choice per direction.
+ * times each compiled tile shape `reps` times on the current state and keeps
+ * the fastest for this context.  Shapes (variant: lines x cells per CTA):
+ * 0: 2x63, 1: 8x15, 2: 4x31, 3: 1x127, 4: 1x95, 5: flat, 128 consecutive
+ * faces of the line-after-line face sequence (a tile may end one line and
+ * start the next; lines shorter than 127 cells take variant 3).  Defaults:
+ * FP64 5 in every direction; FP32 and mixed 3 along x, 1 across.
+ * variants[3] (if not NULL) receives the choice per direction.
  * The state is not changed; the step graphs are rebuilt on next use.
  * Synchronizes. */
 weno_status weno_autotune(weno_ctx* ctx, int reps, int* variants);
 
-/* Pin the tile shape of every sweep direction (variants[d] in 0..4, see
+/* Pin the tile shape of every sweep direction (variants[d] in 0..5, see
  * weno_autotune; ignored in 1D).  Results do not depend on the tile shape:
  * every face is computed by the same arithmetic.  WENO_ERR_INVALID_ARG for
  * an unknown variant. */
@@ -314,6 +317,14 @@ const char* weno_last_error(const weno_ctx* ctx);
  * 1 = float, from a dependent-chain kernel that fills every SM.  Writes the
  * rate to *flops and the kernel time in seconds to *seconds.  Synchronizes. */
 weno_status weno_measure_fma_peak(int precision, double* flops, double* seconds);
+
+/* Diagnostic (no counterpart in the paper): evaluates, for n doubles x_dev[i]
+ * on the device, the Newton-refined reciprocal that the FP64 sweeps use (Roe
+ * average, weight denominator of Eq. eq8-r) next to CUDA's correctly rounded
+ * 1.0 / x, so that tests can bound its error.  out_dev (device, 2 n doubles,
+ * caller-owned) receives [rcp_newton(x) | 1/x].  n < 0, or null pointers
+ * with n > 0: WENO_ERR_INVALID_ARG.  Synchronizes the device. */
+weno_status weno_arith_selftest(const double* x_dev, long long n, double* out_dev);
 
 #ifdef __cplusplus
 }

@@ -425,10 +425,10 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
         return WENO_ERR_CUDA;
     }
     std::memset(ctx->tm_host, 0, sizeof(DevTime));
-    // default tiles (measured on GB300): single long lines in FP64 (ALU
-    // bound, least halo work); coalesced 8-column rows for the float y/z
-    // sweeps
-    for (int d = 0; d < dim; ++d) ctx->tile[d] = (ctx->prec == WENO_FP64 || d == 0) ? 3 : 1;
+    // default tiles, measured measured on the 2048 x 512 double Mach reflection: FP64 flat
+    // 128-face tiles (ALU bound, every lane busy), FP32 1 x 127 along x and
+    // 8 x 15 across (coalesced rows); weno_autotune refines them per state
+    for (int d = 0; d < dim; ++d) ctx->tile[d] = ctx->prec == WENO_FP64 ? 5 : (d == 0 ? 3 : 1);
     if (dim == 1) ctx->tile[0] = 0;
     *out = ctx;
     return WENO_OK;
@@ -897,4 +897,27 @@ extern "C" weno_status weno_measure_fma_peak(int precision, double* flops, doubl
     if (flops) *flops = fl / (best * 1e-3);
     if (seconds) *seconds = best * 1e-3;
     return WENO_OK;
+}
+
+// ------------------------------------------------ arithmetic self-test
+__global__ void k_arith_selftest(const double* x, long long n, double* out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        out[i] = wis::rcp_newton(v);
+        out[n + i] = 1.0 / v;
+    }
+}
+
+extern "C" weno_status weno_arith_selftest(const double* x_dev, long long n, double* out_dev)
+{
+    if (n < 0 || (n > 0 && (x_dev == nullptr || out_dev == nullptr))) return WENO_ERR_INVALID_ARG;
+    if (n == 0) return WENO_OK;
+    const long long want = (n + 255) / 256;
+    const int blocks = (int)(want < 4096 ? want : 4096);
+    k_arith_selftest<<<blocks, 256>>>(x_dev, n, out_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e == cudaSuccess ? WENO_OK : WENO_ERR_CUDA;
 }

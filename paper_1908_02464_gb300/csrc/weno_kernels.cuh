@@ -154,11 +154,13 @@ struct FaceRec {
 // WENO faces are processed in chunks of QC queued faces.
 template <int DIM> struct Chunk { static constexpr int QC = 16; };
 
-template <typename T, int DIM, int LINES, int SEG>
+template <typename T, int DIM, int LINES, int SEG, bool FLAT = false>
 struct SweepSmem {
     static constexpr int CELLS = SEG + 6;
     static constexpr int FACES = SEG + 1;
-    static constexpr int NCELL = LINES * CELLS;
+    // a flat tile may hold the end of one line and the start of the next,
+    // each with its own three-cell halos: five cells more than one segment
+    static constexpr int NCELL = FLAT ? SEG + 11 : LINES * CELLS;
     static constexpr int NFACE = LINES * FACES;
     static constexpr int NQ = CellLayout<DIM>::NQ;
     static constexpr int NV = DIM + 2;
@@ -190,13 +192,21 @@ __device__ __forceinline__ T fifth_difference(T u0, T u1, T u2, T u3, T u4, T u5
 // mode only).  Returns true in every thread whose cells failed the
 // admissibility check.  Ends with a barrier, so tiles can be chained by one
 // CTA (the batched solver) reusing the same shared memory.
-template <typename T, int DIM, int DIR, int LINES, int SEG, int NT, bool EXACTDET>
+//
+// Regular tiles hold LINES lines of SEG cells starting at cell seg_blk * SEG.
+// A flat tile (LINES = 1, lines of at least SEG cells) holds SEG + 1
+// consecutive faces of the sequence of all lines' faces (line after line,
+// nd + 1 faces each), starting at face seg_blk * SEG: every tile computes a
+// full set of faces, and a tile that reaches the end of a line continues on
+// the next one, each piece with its own halo.  line0 and pb are unused then.
+template <typename T, int DIM, int DIR, int LINES, int SEG, int NT, bool EXACTDET, bool FLAT = false>
 __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int line0, int pb, T dt,
                                            unsigned char* smem_raw)
 {
+    static_assert(!FLAT || LINES == 1, "flat tiles hold one line piece at a time");
     using CL = CellLayout<DIM>;
     using FR = FaceRec<T, DIM>;
-    using SM = SweepSmem<T, DIM, LINES, SEG>;
+    using SM = SweepSmem<T, DIM, LINES, SEG, FLAT>;
     constexpr int NV = DIM + 2;
     constexpr int NQ = CL::NQ;
     constexpr int CELLS = SM::CELLS, FACES = SM::FACES;
@@ -223,6 +233,41 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
 
     const T* Ug = reinterpret_cast<const T*>(a.U);
 
+    // flat tiles: piece A = faces fA0 .. fA0 + nA - 1 of line LA, piece B =
+    // faces 0 .. nB - 1 of line LA + 1; in shared memory piece B's cells
+    // follow piece A's, so the stencil of face f starts at cell f (piece A)
+    // or f + 5 (piece B)
+    const int FPL = nd + 1;
+    long long LA = 0, Ftot = 0, F0 = 0;
+    int fA0 = 0, nA = NFACE, nB = 0;
+    if constexpr (FLAT) {
+        const long long nl = DIR == 0 ? (long long)a.n[1] * a.n[2]
+                                      : (DIR == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
+        Ftot = nl * FPL;
+        F0 = (long long)seg_blk * SEG;
+        LA = F0 / FPL;
+        fA0 = (int)(F0 - LA * FPL);
+        nA = FPL - fA0 < NFACE ? FPL - fA0 : NFACE;
+        nB = LA + 1 < nl ? NFACE - nA : 0;
+    }
+    // base address and in-plane index (row j for x sweeps, column i for y/z
+    // sweeps) of line li of a flat tile
+    auto flat_line = [&](long long li, int& inplane) -> long long {
+        if (DIR == 0) {
+            const int j = (int)(li % a.n[1]), kk = (int)(li / a.n[1]);
+            inplane = j;
+            return a.off0 + (long long)j * a.sy + (long long)kk * a.sz;
+        } else if (DIR == 1) {
+            const int i = (int)(li % a.n[0]), kk = (int)(li / a.n[0]);
+            inplane = i;
+            return a.off0 + i + (long long)kk * a.sz;
+        } else {
+            const int i = (int)(li % a.n[0]), j = (int)(li / a.n[0]);
+            inplane = i;
+            return a.off0 + i + (long long)j * a.sy;
+        }
+    };
+
     if (threadIdx.x == 0) { qcount = 0; wcount = 0u; }
 
     // ---- stage the tile (cells c0-3 .. c0+SEG+2 of LINES lines) --------
@@ -232,7 +277,17 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
 #pragma unroll
         for (int k = 0; k < NQ; ++k) cq[k * NCELL + idx] = q[k];
     };
-    if (c0 >= 3 && c0 + SEG + 3 <= nd) {
+    if constexpr (FLAT) {
+        const int nCA = nA + 5, nCB = nB > 0 ? nB + 5 : 0;
+        for (int idx = threadIdx.x; idx < nCA + nCB; idx += NT) {
+            const bool inA = idx < nCA;
+            int inplane;
+            const long long base = flat_line(inA ? LA : LA + 1, inplane);
+            T U[NV];
+            stage_cell<T, DIM, DIR>(a, Ug, base, inplane, inA ? fA0 - 3 + idx : idx - nCA - 3, nd, U);
+            put(idx, U);
+        }
+    } else if (c0 >= 3 && c0 + SEG + 3 <= nd) {
         // the whole halo is interior (uniform over the block)
         for (int idx = threadIdx.x; idx < NCELL; idx += NT) {
             int l, p;
@@ -270,8 +325,9 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
     // sweeps, across the lines (x fastest) for y/z sweeps; consecutive
     // threads read consecutive words in both cases
     auto cidx = [](int l, int p) -> int { return DIR == 0 ? l * CELLS + p : p * LINES + l; };
-    auto fdec = [](int f, int& l, int& p) {
-        if (DIR == 0) { l = f / FACES; p = f - l * FACES; }
+    auto fdec = [&](int f, int& l, int& p) {
+        if constexpr (FLAT) { l = 0; p = f < nA ? f : f + 5; }
+        else if (DIR == 0) { l = f / FACES; p = f - l * FACES; }
         else { p = f / LINES; l = f - p * LINES; }
     };
 
@@ -288,7 +344,8 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
         bool valid = f < NFACE;
         if (valid) {
             fdec(f, l, p);
-            valid = (line0 + l < nline) && (c0 + p <= nd);
+            if constexpr (FLAT) valid = f < nA + nB;
+            else valid = (line0 + l < nline) && (c0 + p <= nd);
         }
         bool weno = false;
         if (valid) {
@@ -377,16 +434,25 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
                 fr[FR::MASK * NFACE + f] = T(a.hybrid == 2 ? fmask : 0);
             }
             // a face is owned by the tile left of it, the last face by the last tile
-            const int face = c0 + p;
-            const bool owned = (p < SEG) || (face == nd);
+            int face = c0 + p;
+            bool owned = (p < SEG) || (face == nd);
+            if constexpr (FLAT) {
+                face = f < nA ? fA0 + f : f - nA;
+                owned = (f < SEG) || (F0 + f == Ftot - 1);
+            }
             if (owned) {
                 if (weno) ++my_weno;
                 if (a.flags != nullptr) {
-                    const int line = line0 + l;
+                    int line = line0 + l, pbf = pb;
+                    if constexpr (FLAT) {
+                        const long long li = f < nA ? LA : LA + 1;
+                        if (DIR == 0) { line = (int)(li % a.n[1]); pbf = (int)(li / a.n[1]); }
+                        else { line = (int)(li % a.n[0]); pbf = (int)(li / a.n[0]); }
+                    }
                     long long fidx;
-                    if (DIR == 0) fidx = ((long long)pb * a.n[1] + line) * (long long)(nd + 1) + face;
-                    else if (DIR == 1) fidx = ((long long)pb * (nd + 1) + face) * (long long)a.n[0] + line;
-                    else fidx = ((long long)face * a.n[1] + pb) * (long long)a.n[0] + line;
+                    if (DIR == 0) fidx = ((long long)pbf * a.n[1] + line) * (long long)(nd + 1) + face;
+                    else if (DIR == 1) fidx = ((long long)pbf * (nd + 1) + face) * (long long)a.n[0] + line;
+                    else fidx = ((long long)face * a.n[1] + pbf) * (long long)a.n[0] + line;
                     a.flags[fidx] = weno ? 0 : 1;
                 }
             }
@@ -496,12 +562,26 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
         int l, p;
         if (DIR == 0) { l = idx / SEG; p = idx - l * SEG; }
         else { p = idx / LINES; l = idx - p * LINES; }
-        const int line = line0 + l;
-        const int cell = c0 + p;
-        if (line >= nline || cell >= nd) continue;
-        const long long g = a.off0 + (long long)line * sl + (long long)pb * sp + (long long)cell * sd;
-        const int fl = DIR == 0 ? l * FACES + p : p * LINES + l;
-        const int fr_ = DIR == 0 ? fl + 1 : fl + LINES;
+        long long g;
+        int fl, fr_, cpos;   // left and right face, stencil start of the left face
+        if constexpr (FLAT) {
+            // the cell between faces idx and idx + 1 of the same piece
+            const bool inA = idx + 1 < nA;
+            if (!inA && (idx < nA || idx + 1 >= nA + nB)) continue;   // line junction or past the end
+            int inplane;
+            g = flat_line(inA ? LA : LA + 1, inplane) + (long long)(inA ? fA0 + idx : idx - nA) * sd;
+            fl = idx;
+            fr_ = idx + 1;
+            cpos = inA ? idx : idx + 5;
+        } else {
+            const int line = line0 + l;
+            const int cell = c0 + p;
+            if (line >= nline || cell >= nd) continue;
+            g = a.off0 + (long long)line * sl + (long long)pb * sp + (long long)cell * sd;
+            fl = DIR == 0 ? l * FACES + p : p * LINES + l;
+            fr_ = DIR == 0 ? fl + 1 : fl + LINES;
+            cpos = p;
+        }
         T rv[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) rv[v] = (fh[v * NFACE + fl] - fh[v * NFACE + fr_]) * inv_dx;
@@ -515,7 +595,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
 #pragma unroll
             for (int v = 0; v < NV; ++v) outp[g + v * a.sv] = (accp ? accp[g + v * a.sv] : T(0)) + rv[v];
         } else {
-            const int ci = cidx(l, p + 3);
+            const int ci = FLAT ? cpos + 3 : cidx(l, cpos + 3);
             T nu[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -538,7 +618,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
     return bad;
 }
 
-template <typename T, int DIM, int DIR, int LINES, int SEG, int NT, bool EXACTDET>
+template <typename T, int DIM, int DIR, int LINES, int SEG, int NT, bool EXACTDET, bool FLAT = false>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
 {
     if (a.tm != nullptr) {
@@ -546,11 +626,12 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int seg_blk, line0, pb;
-    if (DIR == 0) { seg_blk = blockIdx.x; line0 = blockIdx.y * LINES; pb = blockIdx.z; }
+    if (FLAT) { seg_blk = blockIdx.x; line0 = 0; pb = 0; }
+    else if (DIR == 0) { seg_blk = blockIdx.x; line0 = blockIdx.y * LINES; pb = blockIdx.z; }
     else if (DIR == 1) { seg_blk = blockIdx.y; line0 = blockIdx.x * LINES; pb = blockIdx.z; }
     else { seg_blk = blockIdx.z; line0 = blockIdx.x * LINES; pb = blockIdx.y; }
     const T dt = a.mode == MODE_COMBINE ? T(a.tm->dt) : T(0);
-    const bool bad = sweep_tile<T, DIM, DIR, LINES, SEG, NT, EXACTDET>(a, seg_blk, line0, pb, dt, smem_raw);
+    const bool bad = sweep_tile<T, DIM, DIR, LINES, SEG, NT, EXACTDET, FLAT>(a, seg_blk, line0, pb, dt, smem_raw);
     if (bad) atomicOr(&a.tm->status, 1);
 }
 

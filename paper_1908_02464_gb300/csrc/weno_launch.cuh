@@ -22,20 +22,25 @@ namespace wis {
 // rows.  weno_autotune times the variants on a live state and keeps the best.
 //   3 single  1 x 127 halo work ~5%
 //   4 small   1 x 95  96-thread CTAs (more resident CTAs per SM)
-constexpr int kTileVariants = 5;
+//   5 flat    128 consecutive faces of the line-after-line face sequence: no
+//             partly filled tile at the end of each line (512 cells = 4 x 127
+//             + 4 leaves a 4-cell tile per line otherwise); lines shorter
+//             than 127 cells take variant 3 instead
+constexpr int kTileVariants = 6;
 template <int V> struct Tile;
-template <> struct Tile<0> { static constexpr int LINES = 2, SEG = 63, NT = 128; };
-template <> struct Tile<1> { static constexpr int LINES = 8, SEG = 15, NT = 128; };
-template <> struct Tile<2> { static constexpr int LINES = 4, SEG = 31, NT = 128; };
-template <> struct Tile<3> { static constexpr int LINES = 1, SEG = 127, NT = 128; };
-template <> struct Tile<4> { static constexpr int LINES = 1, SEG = 95, NT = 96; };
-struct Tile1D { static constexpr int LINES = 1, SEG = 127, NT = 128; };
+template <> struct Tile<0> { static constexpr int LINES = 2, SEG = 63, NT = 128; static constexpr bool FLAT = false; };
+template <> struct Tile<1> { static constexpr int LINES = 8, SEG = 15, NT = 128; static constexpr bool FLAT = false; };
+template <> struct Tile<2> { static constexpr int LINES = 4, SEG = 31, NT = 128; static constexpr bool FLAT = false; };
+template <> struct Tile<3> { static constexpr int LINES = 1, SEG = 127, NT = 128; static constexpr bool FLAT = false; };
+template <> struct Tile<4> { static constexpr int LINES = 1, SEG = 95, NT = 96; static constexpr bool FLAT = false; };
+template <> struct Tile<5> { static constexpr int LINES = 1, SEG = 127, NT = 128; static constexpr bool FLAT = true; };
+struct Tile1D { static constexpr int LINES = 1, SEG = 127, NT = 128; static constexpr bool FLAT = false; };
 
 template <typename T, int DIM, int DIR, bool EXACTDET, typename TL>
 cudaError_t launch_sweep_one(const SweepArgs& a, cudaStream_t s)
 {
-    using SM = SweepSmem<T, DIM, TL::LINES, TL::SEG>;
-    auto kern = k_sweep<T, DIM, DIR, TL::LINES, TL::SEG, TL::NT, EXACTDET>;
+    using SM = SweepSmem<T, DIM, TL::LINES, TL::SEG, TL::FLAT>;
+    auto kern = k_sweep<T, DIM, DIR, TL::LINES, TL::SEG, TL::NT, EXACTDET, TL::FLAT>;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
@@ -47,7 +52,13 @@ cudaError_t launch_sweep_one(const SweepArgs& a, cudaStream_t s)
     const int nd = a.n[DIR];
     const int segs = (nd + TL::SEG - 1) / TL::SEG;
     dim3 grid;
-    if (DIR == 0) grid = dim3(segs, (a.n[1] + TL::LINES - 1) / TL::LINES, a.n[2]);
+    if (TL::FLAT) {
+        // tile t holds faces t SEG .. t SEG + SEG of the (nd + 1) x lines face sequence
+        const long long lines = DIR == 0 ? (long long)a.n[1] * a.n[2]
+                                         : (DIR == 1 ? (long long)a.n[0] * a.n[2] : (long long)a.n[0] * a.n[1]);
+        const long long faces = (long long)(nd + 1) * lines;
+        grid = dim3((unsigned)((faces - 1 + TL::SEG - 1) / TL::SEG));
+    } else if (DIR == 0) grid = dim3(segs, (a.n[1] + TL::LINES - 1) / TL::LINES, a.n[2]);
     else if (DIR == 1) grid = dim3((a.n[0] + TL::LINES - 1) / TL::LINES, segs, a.n[2]);
     else grid = dim3((a.n[0] + TL::LINES - 1) / TL::LINES, a.n[1], segs);
     kern<<<grid, TL::NT, SM::bytes, s>>>(a);
@@ -61,6 +72,10 @@ cudaError_t launch_sweep_v(int variant, const SweepArgs& a, cudaStream_t s)
     if (variant == 2) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<2>>(a, s);
     if (variant == 3) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<3>>(a, s);
     if (variant == 4) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<4>>(a, s);
+    if (variant == 5) {
+        if (a.n[DIR] >= Tile<5>::SEG) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<5>>(a, s);
+        return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<3>>(a, s);
+    }
     return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<0>>(a, s);
 }
 

@@ -75,6 +75,7 @@ SIGNATURES = {
     "weno_get_time": (ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     "weno_last_error": (ctypes.c_char_p, [_vp]),
     "weno_measure_fma_peak": (ctypes.c_int, [_ip, _dp, _dp]),
+    "weno_arith_selftest": (ctypes.c_int, [_vp, ctypes.c_longlong, _vp]),
     "weno_enqueue_steps": (ctypes.c_int, [_vp, ctypes.c_double, _ip]),
     "weno_autotune": (ctypes.c_int, [_vp, _ip, ctypes.POINTER(_ip)]),
     "weno_batch_create": (ctypes.c_int, [ctypes.POINTER(weno_batch_desc), ctypes.POINTER(weno_params), _vp,
@@ -211,6 +212,16 @@ def weno_measure_fma_peak(precision: int = 0):
     s = ctypes.c_double(0.0)
     _check(load().weno_measure_fma_peak(int(precision), ctypes.byref(f), ctypes.byref(s)))
     return f.value, s.value
+
+
+def weno_arith_selftest(x_dev):
+    """[rcp_newton(x), 1/x] of a float64 CUDA tensor as a (2, n) float64 CUDA
+    tensor (diagnostic of the sweep arithmetic)."""
+    import torch
+    x = x_dev.contiguous()
+    out = torch.empty((2, x.numel()), dtype=torch.float64, device=x.device)
+    _check(load().weno_arith_selftest(_vp(_ptr(x)), int(x.numel()), _vp(_ptr(out))))
+    return out
 
 
 def weno_conserved_totals_noalloc(dim: int, n, dx, precision: str, U_dev, totals_dev, stream: int = 0) -> None:
