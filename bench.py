@@ -288,6 +288,7 @@ def run_ours(args) -> dict:
     batch = None if args.no_batch else batched_riemann(args)
     vortex = None if args.no_vortex else vortex3d_rhs_vjp(args)
     jet = None if args.no_jet else mach2000_jet_run(args)
+    shu = None if args.no_shu else shu_osher_precisions(args)
 
     launches_per_step = 3 + 3 * 2 + 1   # cfl, dt, post, 3 stages x 2 sweeps, set_tend
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -308,6 +309,8 @@ def run_ours(args) -> dict:
         res["vortex3d_256"] = vortex
     if jet is not None:
         res["mach2000_jet"] = jet
+    if shu is not None:
+        res["shu_osher_400"] = shu
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
     if ws > 1:
@@ -354,6 +357,34 @@ def batched_riemann(args) -> dict:
             entry["l1_rho_vs_fp64_max"] = float(np.max(l1))
         out[prec] = entry
         b.close()
+    return out
+
+
+def shu_osher_precisions(args) -> dict:
+    """Shock / entropy-wave interaction (Sec. 4.4 shifted to [-5, 5]) at 400
+    cells to t = 1.8 in FP64, FP32 and mixed: L1 / Linf error of density
+    against the oracle's 3200-cell solution stored in tests/golden, and the
+    wall time of the run (launch-bound at this size)."""
+    import torch
+    from paper_1908_02464_gb300 import problems as P
+    from paper_1908_02464_gb300 import weno
+    path = os.path.join(ROOT, "tests", "golden", "shu_osher_rho_ref400.txt")
+    ref = np.array([float(l) for l in open(path) if not l.startswith("#")])
+    prob, U = P.shu_osher(400)
+    out = {"cells": 400, "t_end": prob["t_end"],
+           "reference": "FP64 oracle on 3200 cells averaged onto 400 (tests/golden/shu_osher_rho_ref400.txt)"}
+    for prec in ("fp64", "fp32", "mixed"):
+        s = weno.Solver(prob, prec)
+        s.set_state(U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = s.advance(prob["t_end"])
+        wall = time.perf_counter() - t0
+        V, _ = s.get_state()
+        s.close()
+        r = V[0].astype(np.float64)
+        out[prec] = {"l1_rho": float(np.mean(np.abs(r - ref))), "linf_rho": float(np.max(np.abs(r - ref))),
+                     "steps": k, "wall_s": wall, "cell_updates_per_s": 3.0 * 400 * k / wall}
     return out
 
 
@@ -510,6 +541,7 @@ def main():
     ap.add_argument("--no-vortex", action="store_true")
     ap.add_argument("--vortex-n", type=int, default=256)
     ap.add_argument("--no-jet", action="store_true")
+    ap.add_argument("--no-shu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -252,3 +252,39 @@ def test_mach2000_jet_matches_sec_4_7():
         assert (g - 1.0) * (bs[3] - 0.5 * bs[1] ** 2 / bs[0]) == pytest.approx(st[3], rel=1e-9)
     assert prob["bc_lo"] == [P.BC_JET, P.BC_REFLECT]
     assert prob["bc_hi"] == [P.BC_TRANSMISSIVE, P.BC_TRANSMISSIVE]
+
+
+# ------------------------------------------ Shu-Osher high-resolution reference
+
+def _shu_osher_ref():
+    vals = [float(l) for l in open(os.path.join(GOLD, "shu_osher_rho_ref400.txt")) if not l.startswith("#")]
+    return np.array(vals)
+
+
+def test_shu_osher_reference_file_is_the_oracles():
+    """The stored 3200-cell reference is what the committed generator computes
+    with the oracle (rounding differences between compilers aside)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("mkref", os.path.join(GOLD, "make_shu_osher_reference.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    rho, _ = mk.reference()
+    ref = _shu_osher_ref()
+    assert ref.shape == (400,)
+    assert np.max(np.abs(rho - ref)) <= 1e-9
+
+
+def test_shu_osher_400_converges_toward_the_reference():
+    """The 400-cell oracle run is close to the 3200-cell reference (the
+    entropy waves behind the shock are the resolution-limited part), and a
+    200-cell run is farther away."""
+    ref = _shu_osher_ref()
+    errs = {}
+    for n in (200, 400):
+        prob, U = P.shu_osher(n)
+        U = np.ascontiguousarray(U)
+        st, t, _ = orc.advance(prob, U, 0.0, prob["t_end"])
+        assert st == 0
+        r = ref if n == 400 else ref.reshape(200, 2).mean(axis=1)
+        errs[n] = np.mean(np.abs(U[0] - r))
+    assert errs[400] < 0.05 and errs[400] < 0.6 * errs[200], errs

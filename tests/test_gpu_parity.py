@@ -464,3 +464,39 @@ def test_measure_fma_peak_runs():
     f64, s64 = weno.weno_measure_fma_peak(0)
     f32, s32 = weno.weno_measure_fma_peak(1)
     assert f64 > 1e11 and f32 > 1e13 and s64 > 0 and s32 > 0
+
+
+def _shu_osher_reference():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "shu_osher_rho_ref400.txt")
+    return np.array([float(l) for l in open(path) if not l.startswith("#")])
+
+
+def test_shu_osher_precisions_against_the_high_resolution_reference():
+    """Shock / entropy-wave interaction at 400 cells to t = 1.8 in FP64, FP32
+    and mixed precision against the oracle's 3200-cell solution (stored in
+    tests/golden by its generator): FP64 has the oracle's own 400-cell error,
+    the reduced precisions stay within 1e-4 (L1 of density) of FP64."""
+    ref = _shu_osher_reference()
+    prob, U = P.shu_osher(400)
+    Uo = np.ascontiguousarray(U.copy())
+    st, to, ko = orc.advance(prob, Uo, 0.0, prob["t_end"])
+    assert st == 0
+    e_or = np.mean(np.abs(Uo[0] - ref))
+    res = {}
+    for prec in ("fp64", "fp32", "mixed"):
+        s = weno.Solver(prob, prec)
+        s.set_state(U)
+        k = s.advance(prob["t_end"])
+        V, t = s.get_state()
+        s.close()
+        assert t == pytest.approx(prob["t_end"], rel=1e-12)
+        r = V[0].astype(np.float64)
+        res[prec] = (r, np.mean(np.abs(r - ref)), np.max(np.abs(r - ref)), k)
+    print("shu-osher 400 vs 3200-cell oracle: oracle-400 L1 %.4e; " % e_or +
+          "; ".join("%s L1 %.4e Linf %.4e steps %d" % (p, v[1], v[2], v[3]) for p, v in res.items()))
+    assert res["fp64"][3] == ko
+    assert abs(res["fp64"][1] - e_or) <= 1e-10
+    for prec in ("fp32", "mixed"):
+        assert np.mean(np.abs(res[prec][0] - res["fp64"][0])) <= 1e-4
+        assert res[prec][1] <= 1.05 * res["fp64"][1]
