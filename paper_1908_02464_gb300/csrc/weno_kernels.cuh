@@ -742,13 +742,14 @@ template <typename T, int DIM>
 __device__ __forceinline__ bool cell_speed(const T* u, T gamma, const T* inv_dx, T& s)
 {
     const T gm1 = gamma - T(1);
-    const T irho = Ar<T>::rcp(u[0]);
+    const T irho = Ar<T>::rcp_f(u[0]);
     T ke2 = T(0);
     T vel[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) { vel[d] = u[1 + d] * irho; ke2 = fmaT(u[1 + d], vel[d], ke2); }
     const T p = gm1 * fmaT(T(-0.5), ke2, u[DIM + 1]);
-    const T c = Ar<T>::sqrt_(gamma * p * irho);
+    const T c2 = gamma * p * irho;
+    const T c = c2 * Ar<T>::rsqrt_(c2);   // NaN for p <= 0, rejected below
     s = T(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) s = fmaT(absT(vel[d]) + c, inv_dx[d], s);
