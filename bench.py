@@ -62,6 +62,12 @@ def measured_peaks() -> dict:
     return {}
 
 
+def nsm_sm_max(torch) -> float:
+    """SM count x maximum SM clock in Hz (the clock from MEASURED_PEAKS.json)."""
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return nsm * float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -335,6 +341,7 @@ def batched_riemann(args) -> dict:
         U0 = b.pack(states)
         U = U0.clone()
         choice = b.autotune(U, trial_steps=3)
+        b.weno_faces(reset=True)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -343,10 +350,22 @@ def batched_riemann(args) -> dict:
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         st, steps, t = b.results()
+        wf = b.weno_faces()
         cu = 3.0 * float(np.sum(params["N"] * steps))
+        # algorithmic flops of the sweeps (oracle operation counts, 1D): per
+        # stage N cells, N + 1 faces, and the counted WENO faces
+        fc, fu, fw = ALG_FLOPS[1]
+        stage_units = 3.0 * steps.astype(np.float64)
+        fl = float(np.sum(stage_units * (params["N"] * (fc + 2 * 3) + (params["N"] + 1) * fu))) + wf * (fw - fu)
+        peak = nsm_sm_max(torch) * (FP64_FLOP_PER_CLK_SM if prec == "fp64" else FP32_FLOP_PER_CLK_SM)
         entry = {"value": cu / (ms * 1e-3), "unit": UNIT, "seconds": ms * 1e-3, "cell_updates": cu,
                  "nonphysical_instances": int(np.sum(st != 0)), "tile_variant": choice[0], "ctas": choice[1],
-                 "steps_total": int(steps.sum())}
+                 "steps_total": int(steps.sum()), "weno_faces": int(wf),
+                 "weno_face_fraction": wf / float(np.sum(stage_units * (params["N"] + 1))),
+                 "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": peak / 1e12,
+                              "unit": "TFLOP/s", "frac": fl / (ms * 1e-3) / peak,
+                              "note": "algorithmic sweep flops (oracle counts) of the whole persistent launch "
+                                      "over its event time; CFL reductions not counted"}}
         res = b.unpack(U)
         if prec == "fp64":
             ref = res
@@ -461,14 +480,23 @@ def vortex3d_rhs_vjp(args) -> dict:
                 ts.append(e0.elapsed_time(e1))
             return min(ts)
 
+        s.weno_faces(reset=True)
         ms_rhs = timeit(lambda: s.rhs(Ud, 0.0, out=r))
+        wf = s.weno_faces() / 3.0   # per RHS evaluation (three timed evaluations)
         ms_vjp = timeit(lambda: s.rhs_vjp(Ud, wd, 0.0, out=g))
         s.set_state(Ud)
         s.autotune(2)
         s.enqueue_steps(10.0, 1)
         torch.cuda.synchronize()
         ms_step = timeit(lambda: s.enqueue_steps(10.0, 1))
-        entry = {"rhs_ms": ms_rhs, "rhs_cell_updates_per_s": cells / (ms_rhs * 1e-3),
+        # algorithmic flops of one RHS (three sweeps, oracle operation counts)
+        fc, fu, fw = ALG_FLOPS[3]
+        fl = 3 * (cells * (fc + 2 * 5) + (n + 1) * n * n * fu) + wf * (fw - fu)
+        peak = nsm_sm_max(torch) * (FP64_FLOP_PER_CLK_SM if prec == "fp64" else FP32_FLOP_PER_CLK_SM)
+        entry = {"rhs_roofline": {"bound": "alu", "achieved": fl / (ms_rhs * 1e-3) / 1e12, "peak": peak / 1e12,
+                                  "unit": "TFLOP/s", "frac": fl / (ms_rhs * 1e-3) / peak,
+                                  "weno_face_fraction": wf / (3.0 * (n + 1) * n * n)},
+                 "rhs_ms": ms_rhs, "rhs_cell_updates_per_s": cells / (ms_rhs * 1e-3),
                  "step_ms": ms_step, "step_cell_updates_per_s": 3 * cells / (ms_step * 1e-3),
                  "vjp_ms": ms_vjp, "vjp_cells_per_s": cells / (ms_vjp * 1e-3)}
         gh = g.double().cpu()

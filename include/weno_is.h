@@ -266,6 +266,11 @@ weno_status weno_batch_results(weno_batch* batch, int* status, long long* steps,
  * CTAs launched.  Synchronizes. */
 weno_status weno_batch_autotune(weno_batch* batch, const void* U_dev, int trial_steps, int* choice);
 
+/* Number of faces computed with the WENO (non-linear) flux by the batch's
+ * runs (autotuner trial runs included) since creation or the last call with
+ * reset != 0; a face counts once per RK stage.  Synchronizes. */
+weno_status weno_batch_weno_face_count(weno_batch* batch, unsigned long long* count, int reset);
+
 void weno_batch_destroy(weno_batch* batch);
 const char* weno_batch_last_error(const weno_batch* batch);
 

@@ -3,11 +3,13 @@
 //
 // Step sequence (one RK3 step, Sec. 4 of the paper) on three rotating state
 // buffers (cur, x, y) selected by phase = completed steps mod 3:
-//   k_cfl(cur) -> k_dt
-//   stage 1: ghosts(cur, t)        sweeps(cur)         -> x = cur + dt L(cur)
-//   stage 2: ghosts(x, t+dt)       sweeps(x), base cur -> y = 3/4 cur + 1/4 (x + dt L(x))
-//   stage 3: ghosts(y, t+dt/2)     sweeps(y), base cur -> x = 1/3 cur + 2/3 (y + dt L(y))
+//   k_cfl(cur) -> k_dt (dt, and the boundary times t, t+dt, t+dt/2)
+//   stage 1: sweeps(cur)         -> x = cur + dt L(cur)
+//   stage 2: sweeps(x), base cur -> y = 3/4 cur + 1/4 (x + dt L(x))
+//   stage 3: sweeps(y), base cur -> x = 1/3 cur + 2/3 (y + dt L(y))
 //   k_post (t += dt, steps += 1 unless a stage failed)
+// The sweeps take the ghost cells from the boundary conditions at the
+// stage's time while staging their tiles; no ghost-cell kernel runs.
 // The new state is x, i.e. buffer (phase + 1) mod 3.  A failed admissibility
 // check latches the device status; later kernels of the step do nothing, the
 // step is not counted and the state stays in cur.
@@ -692,7 +694,7 @@ weno_status weno_enqueue_steps(weno_ctx* ctx, double t_end, int nsteps)
 }
 
 // mean event time of `reps` launches of the direction-d sweep (ACC_SET on the
-// current state, ghosts already filled); weno faces of one launch to *wf
+// current state at its time); weno faces of one launch to *wf
 static weno_status time_sweep_dir(weno_ctx* ctx, int d, int reps, void* flush_dev, size_t flush_bytes,
                                   cudaEvent_t e0, cudaEvent_t e1, double* ms, unsigned long long* wf)
 {

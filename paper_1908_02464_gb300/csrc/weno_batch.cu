@@ -477,6 +477,20 @@ weno_status weno_batch_results(weno_batch* bt, int* status, long long* steps, do
     return WENO_OK;
 }
 
+weno_status weno_batch_weno_face_count(weno_batch* bt, unsigned long long* count, int reset)
+{
+    if (!bt) return WENO_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    BCK(cudaMemcpyAsync(&v, bt->wcount, sizeof(v), cudaMemcpyDeviceToHost, bt->stream));
+    BCK(cudaStreamSynchronize(bt->stream));
+    if (count) *count = v;
+    if (reset) {
+        BCK(cudaMemsetAsync(bt->wcount, 0, sizeof(unsigned long long), bt->stream));
+        BCK(cudaStreamSynchronize(bt->stream));
+    }
+    return WENO_OK;
+}
+
 weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_steps, int* choice)
 {
     if (!bt || !U_dev || trial_steps < 1) return WENO_ERR_INVALID_ARG;

@@ -1,15 +1,18 @@
 // Kernels of the regularized WENO-IS Euler solver (sm_103a).
 //
 //   k_sweep   one direction of the semi-discrete operator (Eq. goveq5): a
-//             tile of LINES grid lines x SEG cells along the sweep, staged in
-//             shared memory with a 3-cell halo; every face of the tile goes
+//             tile of LINES grid lines x SEG cells along the sweep (or 128
+//             consecutive faces of the line-after-line face sequence),
+//             staged in shared memory with a 3-cell halo whose ghost cells
+//             come from the boundary conditions; every face of the tile goes
 //             through the detector (Eq. eq27-28) and either the optimal
 //             linear upwind flux (Eq. linearupwind) or, after compaction
 //             into a per-tile queue, the characteristic regularized WENO-IS
 //             flux (Sec. 2.4, Eq. eq8-r); the tile then takes the flux
 //             divergence and writes an accumulator, a right-hand side or the
 //             RK3 stage combination (Sec. 4).
-//   k_ghost   three ghost layers of one direction (boundary conditions).
+//   k_ghost   three ghost layers of one direction in memory (boundary
+//             conditions), for the adjoint, which reads its halo from memory.
 //   k_cfl     CFL wave-speed max-reduction and admissibility check.
 //   k_dt, k_post   single-thread time-step bookkeeping on the device.
 //   k_totals  conserved totals, FP64 accumulation.

@@ -82,6 +82,7 @@ SIGNATURES = {
                                          ctypes.POINTER(_vp)]),
     "weno_batch_run": (ctypes.c_int, [_vp, _vp]),
     "weno_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(_ip), ctypes.POINTER(ctypes.c_longlong), _dp]),
+    "weno_batch_weno_face_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong), _ip]),
     "weno_batch_autotune": (ctypes.c_int, [_vp, _vp, _ip, ctypes.POINTER(_ip)]),
     "weno_batch_destroy": (None, [_vp]),
     "weno_batch_last_error": (ctypes.c_char_p, [_vp]),
@@ -500,6 +501,11 @@ class Batch:
 
     def autotune(self, U_dev, trial_steps: int = 4):
         return weno_batch_autotune(self.handle, U_dev, trial_steps)
+
+    def weno_faces(self, reset: bool = False) -> int:
+        c = ctypes.c_ulonglong(0)
+        _bcheck(load().weno_batch_weno_face_count(self.handle, ctypes.byref(c), int(reset)), self.handle)
+        return c.value
 
     def close(self):
         if self.handle:

@@ -159,3 +159,33 @@ def test_batch_rejects_bad_descriptions():
     with pytest.raises(weno.WenoError) as e:
         weno.weno_batch_create([100], 0.0, 1.0, [0.1], p, bc_lo=3)
     assert e.value.status == weno.WENO_ERR_INVALID_ARG
+
+
+def test_batch_weno_face_count_equals_single_solver_counts():
+    """The batch counts each WENO face once per RK stage, like the
+    single-problem solver: over instances that finish, the batch's count
+    equals the sum of the single solver's counts."""
+    params, states = _small_batch(count=12, seed=5)
+    counts, ok = [], []
+    for i in range(len(states)):
+        prob, U = P.riemann_instance(params, i)
+        s = weno.Solver(prob, "fp64")
+        s.set_state(U)
+        s.weno_faces(reset=True)
+        try:
+            s.advance(prob["t_end"])
+        except weno.WenoError:
+            s.close()
+            continue
+        counts.append(s.weno_faces())
+        ok.append(i)
+        s.close()
+    assert len(ok) >= 8
+    b = weno.Batch(params["N"][ok], 0.0, 1.0, params["t_end"][ok], "fp64")
+    U = b.pack([states[i] for i in ok])
+    b.weno_faces(reset=True)
+    b.run(U)
+    st, steps, t = b.results()
+    assert np.all(st == 0)
+    assert b.weno_faces() == sum(counts) and sum(counts) > 0
+    b.close()
