@@ -274,6 +274,7 @@ struct VjpArgs {
     int n[3];
     long long sy, sz, sv, off0;
     double inv_dx, eps_h, gamma, eps, c_lambda;
+    double slim;   // 60 sqrt(eps_h), as in the forward sweep
     int hybrid;
 };
 
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
     __syncthreads();
 
     // ---- per face: forward recompute and reverse -------------------------
-    const T lim0 = T(3600.0 * a.eps_h);
+    const T slim = T(a.slim);
     const T lam_k = T(a.c_lambda / 3600.0);
     const T eps = T(a.eps), inv_dx = T(a.inv_dx);
     for (int f = threadIdx.x; f < NF; f += NT) {
@@ -363,10 +364,10 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
         }
         T w[NV];
         proj_all<T, DIM, DIR>(r, dU, w);
-        const T lim = lim0 * (r.rt * r.rt);
+        const T lim = slim * r.rt;
         bool smooth = a.hybrid != 0;
 #pragma unroll
-        for (int s = 0; s < NV; ++s) smooth = smooth && lt_nn(w[s] * w[s], lim);
+        for (int s = 0; s < NV; ++s) smooth = smooth && abs_lt(w[s], lim);
         // LLF speeds and the cells attaining them
         T am = rec(0, CL::LM), a0 = rec(0, CL::L0), ap = rec(0, CL::LP);
         int im = 0, i0 = 0, ip = 0;

@@ -114,7 +114,8 @@ static wis::SweepArgs sweep_args(weno_ctx* c, int dir)
     a.inv_dx_f = (float)(a.inv_dx * (1.0 / 60.0));   // face fluxes are kept times 60
     a.gamma_f = (float)a.gamma;
     a.eps_f = (float)a.eps;
-    a.lim0_f = (float)(3600.0 * a.eps_h);
+    a.slim = std::sqrt(3600.0 * a.eps_h);
+    a.slim_f = (float)a.slim;
     a.lam_scale_f = (float)(a.c_lambda * (1.0 / 3600.0));
     a.bc_lo = c->g.bc_lo[dir];
     a.bc_hi = c->g.bc_hi[dir];
@@ -614,6 +615,7 @@ weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, vo
         a.sy = ctx->sy; a.sz = ctx->sz; a.sv = ctx->sv; a.off0 = ctx->off0;
         a.inv_dx = ctx->inv_dx[d];
         a.eps_h = ctx->eps_h[d];
+        a.slim = std::sqrt(3600.0 * a.eps_h);
         a.gamma = ctx->p.gamma; a.eps = ctx->p.eps; a.c_lambda = ctx->p.c_lambda; a.hybrid = ctx->p.hybrid;
         CK(f64 ? wis::vjp_f64(ctx->dim, d, a, ctx->stream) : wis::vjp_f32(ctx->dim, d, a, ctx->stream));
         wis::GhostArgs ga = ghost_args(ctx, ctx->rhs_out, d);

@@ -99,7 +99,8 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs b)
         a.gamma = b.gamma; a.eps = b.eps; a.c_lambda = b.c_lambda; a.hybrid = b.hybrid;
         a.wmode = b.wmode; a.split = b.split; a.alpha_g = nullptr;
         a.inv_dx_f = (float)(a.inv_dx * (1.0 / 60.0)); a.gamma_f = (float)b.gamma; a.eps_f = (float)b.eps;
-        a.lim0_f = (float)(3600.0 * eps_h); a.lam_scale_f = (float)(b.c_lambda * (1.0 / 3600.0));
+        a.slim = sqrt(3600.0 * eps_h);
+        a.slim_f = (float)a.slim; a.lam_scale_f = (float)(b.c_lambda * (1.0 / 3600.0));
         const T inv_dx_t[1] = {T(a.inv_dx)};
         const int ntiles = (n + SEG - 1) / SEG;
 

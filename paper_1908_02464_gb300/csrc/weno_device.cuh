@@ -167,6 +167,12 @@ __device__ __forceinline__ float max_nn(float a, float b)
 }
 __device__ __forceinline__ bool lt_nn(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
 __device__ __forceinline__ bool lt_nn(float a, float b) { return __float_as_int(a) < __float_as_int(b); }
+// |w| < lim for a non-negative lim, on the bit patterns (integer pipes only)
+__device__ __forceinline__ bool abs_lt(double w, double lim)
+{
+    return (__double_as_longlong(w) & 0x7fffffffffffffffLL) < __double_as_longlong(lim);
+}
+__device__ __forceinline__ bool abs_lt(float w, float lim) { return (__float_as_int(w) & 0x7fffffff) < __float_as_int(lim); }
 
 // w[s] = L^s . x for all fields.
 template <typename T, int DIM, int DIR>
@@ -234,12 +240,12 @@ template <>
 __device__ __forceinline__ double recon<double>(double a, double b, double c, double d, double e,
                                                 double lam, double eps, int wmode)
 {
-    // Eq. eq6
-    const double q0 = 0.5 * (c + d);
-    const double q1 = fmaT(1.5, c, -0.5 * b);
-    const double q2 = fmaT(1.0 / 3.0, c, fmaT(5.0 / 6.0, d, (-1.0 / 6.0) * e));
-    const double q3 = fmaT(1.0 / 3.0, a, fmaT(-7.0 / 6.0, b, (11.0 / 6.0) * c));
-    if (wmode == W_LINEAR) return fmaT(0.4, q0, fmaT(0.2, q1, fmaT(0.3, q2, 0.1 * q3)));
+    // Eq. eq6 with the optimal weights of Eq. eq8 folded in: q_k = d_k fhat_k
+    const double q0 = 0.2 * (c + d);                                              // 0.4 (c + d) / 2
+    const double q1 = fmaT(0.3, c, -0.1 * b);                                     // 0.2 (3c - b) / 2
+    const double q2 = fmaT(0.1, c, fmaT(0.25, d, -0.05 * e));                     // 0.3 (2c + 5d - e) / 6
+    const double q3 = fmaT(1.0 / 30.0, a, fmaT(-7.0 / 60.0, b, (11.0 / 60.0) * c));  // 0.1 (2a - 7b + 11c) / 6
+    if (wmode == W_LINEAR) return (q0 + q1) + (q2 + q3);
     // Eq. eq11
     const double b0 = (d - c) * (d - c);
     const double b1 = (c - b) * (c - b);
@@ -275,15 +281,16 @@ __device__ __forceinline__ double recon<double>(double a, double b, double c, do
             L01 = tau;
         }
     }
-    // sum_k alpha_k q_k / sum_k alpha_k over the common denominator
-    // D_0 D_1 D_2 D_3 (one division)
-    const double D01 = D0 * D1, D23 = D2 * D3;
-    const double w0 = 0.4 * (D0 + L01) * (D1 * D23);
-    const double w1 = 0.2 * (D1 + L01) * (D0 * D23);
-    const double w2 = 0.3 * (D2 + L23) * (D01 * D3);
-    const double w3 = 0.1 * (D3 + L23) * (D01 * D2);
+    // sum_k alpha_k fhat_k / sum_k alpha_k over the common denominator
+    // P = D_0 D_1 D_2 D_3 (one reciprocal): alpha_k P / d_k = (D_k + L) P / D_k
+    // = P + L prod_{j != k} D_j, and the d_k sit in q_k and in the denominator
+    const double D01 = D0 * D1, D23 = D2 * D3, P = D01 * D23;
+    const double w0 = fmaT(L01, D1 * D23, P);
+    const double w1 = fmaT(L01, D0 * D23, P);
+    const double w2 = fmaT(L23, D01 * D3, P);
+    const double w3 = fmaT(L23, D01 * D2, P);
     const double num = fmaT(w0, q0, fmaT(w1, q1, fmaT(w2, q2, w3 * q3)));
-    const double den = (w0 + w1) + (w2 + w3);
+    const double den = fmaT(0.4, w0, fmaT(0.2, w1, fmaT(0.3, w2, 0.1 * w3)));
     return num * rcp_newton(den);
 }
 

@@ -60,13 +60,14 @@ struct SweepArgs {
     int n[3];
     long long sy, sz, sv, off0;
     double inv_dx, eps_h, gamma, eps, c_lambda;
+    double slim;                    // 60 sqrt(eps_h): the detector threshold on |60 dv^s| / rho~
     int hybrid;
     int wmode;                      // W_REG, W_IS, W_WANG, W_LINEAR
     int split;                      // SPLIT_LLF, SPLIT_LF, SPLIT_RF
     const unsigned long long* alpha_g;  // SPLIT_LF: bits of max |u-c|, |u|, |u+c| of this direction
     // the same constants pre-rounded for float kernels (a double conversion
     // or division per thread would run on the slow FP64 pipe)
-    float inv_dx_f, gamma_f, eps_f, lim0_f, lam_scale_f, rk_a_f, rk_b_f;
+    float inv_dx_f, gamma_f, eps_f, slim_f, lam_scale_f, rk_a_f, rk_b_f;
     // boundary conditions of this direction, applied while staging the tile
     // (the ghost cells are computed, not read)
     int bc_lo, bc_hi;
@@ -334,8 +335,8 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
         else { p = f / LINES; l = f - p * LINES; }
     };
 
-    // sigma^s < eps_h  <=>  (60 dv^s)^2 < 3600 eps_h rho~^2
-    const T lim0 = pick<T>(3600.0 * a.eps_h, a.lim0_f);
+    // sigma^s < eps_h  <=>  |60 dv^s| < 60 sqrt(eps_h) rho~ (both sides >= 0)
+    const T slim = pick<T>(a.slim, a.slim_f);
     const T lam_scale = pick<T>(a.c_lambda * (1.0 / 3600.0), a.lam_scale_f);
     const int lane = threadIdx.x & 31;
     unsigned int my_weno = 0;
@@ -371,10 +372,10 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             }
             T w[NV];
             proj_all<T, DIM, DIR>(r, dU, w);
-            const T lim = lim0 * (r.rt * r.rt);
+            const T lim = slim * r.rt;
             int fmask = 0;
 #pragma unroll
-            for (int s = 0; s < NV; ++s) fmask |= lt_nn(w[s] * w[s], lim) ? (1 << s) : 0;
+            for (int s = 0; s < NV; ++s) fmask |= abs_lt(w[s], lim) ? (1 << s) : 0;
             const bool smooth = a.hybrid != 0 && fmask == (1 << NV) - 1;
             // splitting speeds: LLF max over the six stencil cells, global
             // LF maxima, or the Roe-average eigenvalues
