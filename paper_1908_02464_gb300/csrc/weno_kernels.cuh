@@ -432,9 +432,10 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
                 const T irt2 = Ar<T>::rcp(r.rt * r.rt);
 #pragma unroll
                 for (int s = 0; s < NV; ++s) fr[(FR::LAM + s) * NFACE + f] = lam_scale * (w[s] * w[s]) * irt2;
-                fr[FR::AM * NFACE + f] = am;
-                fr[FR::A0 * NFACE + f] = a0;
-                fr[FR::AP * NFACE + f] = ap;
+                // half splitting speeds (Eq. flxuspliting: f+- = (g +- alpha v) / 2)
+                fr[FR::AM * NFACE + f] = T(0.5) * am;
+                fr[FR::A0 * NFACE + f] = T(0.5) * a0;
+                fr[FR::AP * NFACE + f] = T(0.5) * ap;
                 fr[FR::MASK * NFACE + f] = T(a.hybrid == 2 ? fmask : 0);
             }
             // a face is owned by the tile left of it, the last face by the last tile
@@ -507,7 +508,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             for (int s = 0; s < NV; ++s) {
                 const T al = s == 0 ? am : (s == NV - 1 ? ap : a0);
                 const T h = T(0.5) * wg[s];
-                const T k = T(0.5) * al * wv[s];
+                const T k = al * wv[s];   // al holds alpha / 2
                 fpm[((q * NV + s) * 2 + 0) * 6 + m] = h + k;
                 fpm[((q * NV + s) * 2 + 1) * 6 + m] = h - k;
             }
