@@ -522,12 +522,28 @@ def oracle_steps(nsteps: int, U=None, t=0.0):
     return time.perf_counter() - t0, U, t
 
 
+def host_info() -> dict:
+    """Host cores and CPU model, for the CPU-baseline lines."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "hardware", "cpu model"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"host_cores": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
 def cpu_baseline(args) -> dict:
     steps = args.cpu_steps
     el, _, _ = oracle_steps(steps)
     return {"value": 3.0 * NX * NY * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} FP64 RK3 steps of the {NX}x{NY} double Mach reflection from its initial "
-                      f"condition, single-threaded C++ oracle ({el:.1f} s)"}
+                      f"condition, single-threaded C++ oracle ({el:.1f} s)", **host_info()}
 
 
 def run_reference(args) -> dict | None:
@@ -550,7 +566,8 @@ def run_reference(args) -> dict | None:
                                    "condition, LLF splitting, hybrid on, TVD RK3 CFL 0.5",
                        "grid": [NX, NY], "cells": NX * NY, "precision": "fp64"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.warmup}+{args.steps} RK3 steps of the full grid from t=0"},
+                             "sample": f"{args.warmup}+{args.steps} RK3 steps of the full grid from t=0",
+                             **host_info()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
