@@ -731,6 +731,7 @@ struct CflArgs {
     double inv_dx[3];
     double gamma;
     DevTime* tm;
+    int parts;    // k_cfl: x-parts per grid row (rows x parts blocks of work)
 };
 
 __device__ __forceinline__ double warp_max(double v)
@@ -780,25 +781,34 @@ __global__ void __launch_bounds__(256) k_cfl(CflArgs a)
     constexpr int NV = DIM + 2;
     if (a.tm->status != 0) return;
     const T* U = reinterpret_cast<const T*>(a.U);
-    const long long nx = a.n[0], ny = a.n[1];
-    const long long total = nx * ny * (long long)a.n[2];
+    const int nx = a.n[0], ny = a.n[1];
+    const long long rows = (long long)ny * a.n[2];
     const T gamma = T(a.gamma);
     T idx_[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) idx_[k] = T(a.inv_dx[k]);
-    double smax = 0.0;
+    // work unit: one of `parts` x-ranges of one grid row (row indices are
+    // decomposed once per unit, not per cell); the running max of the
+    // non-negative speeds is exact in the storage precision
+    const int span = (nx + a.parts - 1) / a.parts;
+    T smax_t = T(0);
     bool bad = false;
-    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-         id += (long long)gridDim.x * blockDim.x) {
-        const long long i = id % nx, j = (id / nx) % ny, k = id / (nx * ny);
-        const long long g = a.off0 + i + j * a.sy + k * a.sz;
-        T u[NV];
+    for (long long c = blockIdx.x; c < rows * a.parts; c += gridDim.x) {
+        const long long row = c / a.parts;
+        const int part = (int)(c - row * a.parts);
+        const int j = (int)(row % ny), k = (int)(row / ny);
+        const long long gr = a.off0 + (long long)j * a.sy + (long long)k * a.sz;
+        const int x1 = min(nx, (part + 1) * span);
+        for (int i = part * span + threadIdx.x; i < x1; i += blockDim.x) {
+            T u[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) u[v] = U[g + v * a.sv];
-        T s;
-        if (!cell_speed<T, DIM>(u, gamma, idx_, s)) bad = true;
-        else smax = maxT(smax, (double)s);
+            for (int v = 0; v < NV; ++v) u[v] = U[gr + i + v * a.sv];
+            T s;
+            if (!cell_speed<T, DIM>(u, gamma, idx_, s)) bad = true;
+            else smax_t = max_nn(smax_t, s);
+        }
     }
+    double smax = (double)smax_t;
     __shared__ double red[8];
     smax = warp_max(smax);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;

@@ -115,10 +115,18 @@ cudaError_t launch_ghost_t(int dim, const GhostArgs& a, cudaStream_t s)
 }
 
 template <typename T>
-cudaError_t launch_cfl_t(int dim, const CflArgs& a, int nsm, cudaStream_t s)
+cudaError_t launch_cfl_t(int dim, const CflArgs& a_in, int nsm, cudaStream_t s)
 {
-    const long long cells = (long long)a.n[0] * a.n[1] * a.n[2];
-    const int blocks = grid_for(cells, 256, nsm * 8);
+    // rows x parts units of at least 256 cells each, about 8 blocks per SM
+    CflArgs a = a_in;
+    const long long rows = (long long)a.n[1] * a.n[2];
+    const long long want = (long long)nsm * 8;
+    long long parts = (want + rows - 1) / rows;
+    const long long most = (a.n[0] + 255) / 256;
+    if (parts > most) parts = most;
+    if (parts < 1) parts = 1;
+    a.parts = (int)parts;
+    const int blocks = grid_for(rows * parts * 256, 256, nsm * 8);
     if (dim == 1) k_cfl<T, 1><<<blocks, 256, 0, s>>>(a);
     else if (dim == 2) k_cfl<T, 2><<<blocks, 256, 0, s>>>(a);
     else k_cfl<T, 3><<<blocks, 256, 0, s>>>(a);
