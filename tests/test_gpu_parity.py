@@ -358,11 +358,28 @@ def _variant_cases():
     for dim, n in ((2, [150, 37]), (2, [300, 140]), (3, [40, 23, 19]), (3, [130, 9, 128])):
         cases.append(P.random_state(dim, n, seed=77, kind="mixed"))
     # non-periodic boundaries on lines long enough for flat tiles: double Mach
-    # (inflow, wall, moving shock) and the jet inflow
+    # (inflow, wall, moving shock), the jet inflow, and a 3D box with
+    # reflecting and transmissive faces
     prob, U = P.double_mach(200, 130)
     cases.append((prob, U))
     cases.append(P.mach2000_jet(160, 40))
+    cases.append(_box3d_walls())
     return cases
+
+
+def _box3d_walls():
+    prob, U = P.random_state(3, [130, 9, 128], seed=78, kind="mixed")
+    prob["bc_lo"] = [P.BC_REFLECT, P.BC_TRANSMISSIVE, P.BC_REFLECT]
+    prob["bc_hi"] = [P.BC_TRANSMISSIVE, P.BC_REFLECT, P.BC_TRANSMISSIVE]
+    return prob, U
+
+
+def test_rhs_parity_3d_walls_flat_tiles():
+    """3D state with reflecting and transmissive faces, lines of 130 and 128
+    cells (flat tiles along x and z by default, one tile variant down the
+    9-cell y lines)."""
+    prob, U = _box3d_walls()
+    _compare_rhs(prob, U)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
