@@ -246,23 +246,27 @@ __device__ __forceinline__ double recon<double>(double a, double b, double c, do
     const double q2 = fmaT(0.1, c, fmaT(0.25, d, -0.05 * e));                     // 0.3 (2c + 5d - e) / 6
     const double q3 = fmaT(1.0 / 30.0, a, fmaT(-7.0 / 60.0, b, (11.0 / 60.0) * c));  // 0.1 (2a - 7b + 11c) / 6
     if (wmode == W_LINEAR) return (q0 + q1) + (q2 + q3);
-    // Eq. eq11
-    const double b0 = (d - c) * (d - c);
-    const double b1 = (c - b) * (c - b);
-    double t = fmaT(-2.0, d, c) + e;
-    double s = fmaT(-4.0, d, 3.0 * c) + e;
-    const double b2 = fmaT(13.0 / 12.0, t * t, 0.25 * (s * s));
-    t = fmaT(-2.0, b, a) + c;
-    s = fmaT(-4.0, b, a) + 3.0 * c;
-    const double b3 = fmaT(13.0 / 12.0, t * t, 0.25 * (s * s));
-    t = fmaT(-4.0, b + d, a + e) + 6.0 * c;
-    s = fmaT(2.0, b - d, e - a);
+    // Eq. eq11 from shared differences: with d0 = d - c, d1 = c - b,
+    //   c - 2d + e = (e - d) - d0,        3c - 4d + e = (c - 2d + e) - 2 d0,
+    //   a - 2b + c = (a - b) + d1,        a - 4b + 3c = (a - 2b + c) + 2 d1,
+    //   b - 2c + d = d0 - d1,  a - 4b + 6c - 4d + e = (a - 2b + c) - 2 (b - 2c + d) + (c - 2d + e),
+    //   -a + 2b - 2d + e = (e - d) - (a - b) - (d0 + d1)
+    const double d0 = d - c, d1 = c - b;
+    const double b0 = d0 * d0;
+    const double b1 = d1 * d1;
+    const double ed = e - d, ab = a - b;
+    const double t2 = ed - d0, s2 = fmaT(-2.0, d0, t2);
+    const double b2 = fmaT(13.0 / 12.0, t2 * t2, 0.25 * (s2 * s2));
+    const double t3 = ab + d1, s3 = fmaT(2.0, d1, t3);
+    const double b3 = fmaT(13.0 / 12.0, t3 * t3, 0.25 * (s3 * s3));
+    const double te = d0 - d1;
+    double t = fmaT(-2.0, te, t3) + t2;
+    double s = (ed - ab) - (d0 + d1);
     const double tau = fmaT(13.0 / 12.0, t * t, 0.25 * (s * s));
     double D0, D1, D2, D3, L01, L23;
     if (wmode == W_REG) {
         // Eq. eq18 (E_2 = E_3 = 0) and Eq. eq8-r
-        t = fmaT(-2.0, c, b + d);
-        const double E = (t * t) * (1.0 / 45.0);
+        const double E = (te * te) * (1.0 / 45.0);
         D0 = fmaT(lam, b0, E + eps);
         D1 = fmaT(lam, b1, E + eps);
         D2 = fmaT(lam, b2, eps);
