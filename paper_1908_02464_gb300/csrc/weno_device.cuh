@@ -222,6 +222,27 @@ __device__ __forceinline__ void back_proj_add(const Roe<T, DIM>& r, const T* w, 
     out[LAST] += e + eshear;
 }
 
+// out += sum_s R^s alpha^s w^s with w = L dU and the entropy and shear fields
+// sharing one speed a0 (the LLF, global LF and Roe splittings all do): since
+// R w = R L dU = dU, the sum is a0 dU + (am - a0) w_0 R^{u-c} + (ap - a0)
+// w_last R^{u+c}, which needs only the two acoustic eigenvectors.
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void ups_dissipation_add(const Roe<T, DIM>& r, const T* dU, const T* w, T am, T a0,
+                                                    T ap, T* out)
+{
+    constexpr int LAST = DIM + 1;
+    const T k0 = (am - a0) * w[0], k3 = (ap - a0) * w[LAST];
+#pragma unroll
+    for (int v = 0; v <= LAST; ++v) out[v] = fmaT(a0, dU[v], out[v]);
+    // R^{u-+c} = (1, u -+ c n, H -+ u_n c)
+    const T s = k0 + k3, dd = k3 - k0;
+    out[0] += s;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+        out[1 + k] = k == DIR ? fmaT(r.u[k], s, fmaT(r.c, dd, out[1 + k])) : fmaT(r.u[k], s, out[1 + k]);
+    out[LAST] = fmaT(r.H, s, fmaT(r.u[DIR] * r.c, dd, out[LAST]));
+}
+
 // --------------------------------------------------- scalar reconstruction
 // Weight modes: 0 regularized (Eq. eq8-r, the method), 1 WENO-IS (Eq. eq8),
 // 2 WENO-IS of Wang et al. (Eq. eq14-15), 3 optimal linear weights d_k.

@@ -410,12 +410,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
                     const T f23 = cq[k * NCELL + cidx(l, p + 2)] + cq[k * NCELL + cidx(l, p + 3)];
                     Fo[v] = fmaT(T(37), f23, fmaT(T(-8), f14, f05));
                 }
-                T aw[NV];
-                aw[0] = am * w[0];
-#pragma unroll
-                for (int s = 1; s < NV - 1; ++s) aw[s] = a0 * w[s];
-                aw[NV - 1] = ap * w[NV - 1];
-                back_proj_add<T, DIM, DIR>(r, aw, Fo);
+                ups_dissipation_add<T, DIM, DIR>(r, dU, w, am, a0, ap, Fo);
                 // face fluxes are kept times 60; the divergence scales by dx/60
 #pragma unroll
                 for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = Fo[v];
