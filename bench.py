@@ -247,6 +247,7 @@ def run_ours(args) -> dict:
 
     # reduced-precision paths on the same state
     extra = {}
+    flags64 = None
     if not args.fp64_only:
         for prec in ("fp32", "mixed"):
             sp = weno.Solver(prob, prec, stream=stream)
@@ -257,12 +258,20 @@ def run_ours(args) -> dict:
             torch.cuda.nvtx.range_push(f"sweeps_{prec}")
             ms_d, wf_d = sp.time_sweeps(reps=5, flush=flush)
             torch.cuda.nvtx.range_pop()
+            # hybrid-switch decisions against FP64 on the same float-rounded state
+            # (arithmetic only; storage rounding is the same on both sides)
+            Uf = np.ascontiguousarray(U64.astype(np.float32))
+            fl_p = sp.face_flags(torch.from_numpy(Uf).cuda(), t64).cpu().numpy()
+            if flags64 is None:
+                flags64 = s64.face_flags(torch.from_numpy(Uf.astype(np.float64)).cuda(), t64).cpu().numpy()
             dd = int(np.argmax(ms_d))
             flp = sweep_flops(2, [NX, NY], wf_d[dd], dd)
             peak32 = nsm * FP32_FLOP_PER_CLK_SM * sm_max * 1e6
             extra[prec] = {"value": ws * 3.0 * cells * args.steps / (totp * 1e-3), "ms_per_step": totp / args.steps,
                            "l1_rho_vs_fp64": float(np.mean(d)), "linf_rho_vs_fp64": float(np.max(d)),
                            "weno_face_fraction": wfp / (n_faces_step * args.steps),
+                           "hybrid_flags_differing_from_fp64_same_data": int(np.sum(fl_p != flags64)),
+                           "faces": int(flags64.size),
                            "t_after": tp_, "t_fp64_after": t64,
                            "roofline": {"bound": "alu", "achieved": flp / (ms_d[dd] * 1e-3) / 1e12,
                                         "peak": peak32 / 1e12, "unit": "TFLOP/s",

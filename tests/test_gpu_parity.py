@@ -517,3 +517,46 @@ def test_shu_osher_precisions_against_the_high_resolution_reference():
     for prec in ("fp32", "mixed"):
         assert np.mean(np.abs(res[prec][0] - res["fp64"][0])) <= 1e-4
         assert res[prec][1] <= 1.05 * res["fp64"][1]
+
+
+def _flags_by_precision(prob, V, t):
+    """Face flags of FP64, FP32 and mixed on the same float-rounded state."""
+    Vf = V.astype(np.float32)
+    out = {}
+    for prec, data in (("fp64", Vf.astype(np.float64)), ("fp32", Vf), ("mixed", Vf)):
+        s = weno.Solver(prob, prec)
+        out[prec] = s.face_flags(torch.from_numpy(np.ascontiguousarray(data)).cuda(), t).cpu().numpy()
+        s.close()
+    return out
+
+
+def test_reduced_precision_arithmetic_does_not_flip_hybrid_flags():
+    """The hybrid switch compares the detector with eps_h.  The sweeps form
+    the fifth difference from differences of neighbouring cells, which are
+    exact in float (Sterbenz), and small multiples of those; so on the same
+    float-stored data the FP32 and mixed decisions match FP64's.  Checked on a
+    developed double Mach state (eps_h = dx^3) and on a smooth state with
+    eps_h moved to the median detector value (C_thr scaled from the oracle's
+    detector ratios), where half of the faces sit near the threshold.  The
+    flips that float storage of the state itself causes are reported beside."""
+    prob, U = P.double_mach(256, 64)
+    s = weno.Solver(prob, "fp64")
+    s.set_state(U)
+    s.advance(0.02)
+    V, t = s.get_state()
+    s.close()
+    prob2, U2 = P.random_state(2, [256, 64], seed=5, kind="smooth")
+    _, _, ratio = orc.rhs(prob2, U2.astype(np.float32).astype(np.float64), 0.0, want_flags=True)
+    prob2["C_thr"] = float(prob2["C_thr"] * np.median(ratio))
+    for name, pr, st, tt in (("double Mach 256x64", prob, V, t), ("smooth 256x64, median threshold", prob2, U2, 0.0)):
+        fl = _flags_by_precision(pr, st, tt)
+        n = fl["fp64"].size
+        d32 = int(np.sum(fl["fp32"] != fl["fp64"]))
+        dmx = int(np.sum(fl["mixed"] != fl["fp64"]))
+        s = weno.Solver(pr, "fp64")
+        f_orig = s.face_flags(torch.from_numpy(np.ascontiguousarray(st)).cuda(), tt).cpu().numpy()
+        s.close()
+        dst = int(np.sum(fl["fp32"] != f_orig))
+        print(f"{name}: {n} faces, {int(np.sum(fl['fp64'] == 0))} WENO; flags differing from FP64 on the same "
+              f"float data: fp32 {d32}, mixed {dmx}; fp32 against FP64 on the unrounded state: {dst}", flush=True)
+        assert d32 <= 1e-4 * n and dmx <= 1e-4 * n
