@@ -50,8 +50,9 @@ typedef enum {
     WENO_FP64 = 0,   /* all arithmetic and storage in double                    */
     WENO_FP32 = 1,   /* float storage and arithmetic; time step, time and the
                         conserved totals in double                             */
-    WENO_MIXED = 2   /* float storage and bulk arithmetic; the detector and the
-                        hybrid switch (Eq. eq27-28, eq31) in double             */
+    WENO_MIXED = 2   /* as FP32, with the detector's fifth difference
+                        (Eq. eq28), which decides the hybrid switch, formed
+                        as exact nested float differences                      */
 } weno_precision;
 
 /* boundary codes, one per side and direction (ghost cells, three layers).
