@@ -349,7 +349,7 @@ def batched_riemann(args) -> dict:
         b = weno.Batch(params["N"], 0.0, 1.0, params["t_end"], prec)
         U0 = b.pack(states)
         U = U0.clone()
-        choice = b.autotune(U, trial_steps=3)
+        choice = b.autotune(U, trial_steps=8)
         b.weno_faces(reset=True)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -260,11 +260,14 @@ weno_status weno_batch_run(weno_batch* batch, void* U_dev);
  * Synchronizes; returns WENO_ERR_NONPHYSICAL if any instance failed. */
 weno_status weno_batch_results(weno_batch* batch, int* status, long long* steps, double* t);
 
-/* Autotuner (no counterpart in the paper): times trial runs of trial_steps
- * steps per instance on U_dev (not modified) for each CTA size (64, 128, 256
- * threads: tiles of 63, 127, 255 faces) and residency (all that fit, 4 or 2
- * CTAs per SM) and keeps the fastest.  choice[0] = tile variant, choice[1] =
- * CTAs launched.  Synchronizes. */
+/* Autotuner (no counterpart in the paper): times trial runs on U_dev (not
+ * modified) for each CTA size (64, 128, 256 threads: tiles of 63, 127, 255
+ * faces) and residency (all that fit, 4 or 2 CTAs per SM) and keeps the
+ * fastest.  In a trial run instance i takes ceil(trial_steps N_i / N_max)
+ * steps (at least one): a full run's step count grows with the cell count,
+ * so the trial keeps the full run's work per instance, growing like N_i^2,
+ * and with it the load balance of the schedule.  choice[0] = tile variant,
+ * choice[1] = CTAs launched.  Synchronizes. */
 weno_status weno_batch_autotune(weno_batch* batch, const void* U_dev, int trial_steps, int* choice);
 
 /* Number of faces computed with the WENO (non-linear) flux by the batch's

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -42,6 +43,7 @@ struct BatchArgs {
     unsigned int* head;      // work-queue counter (reset before each launch)
     unsigned long long* weno_count;
     int max_steps;
+    const int* trial_caps;   // autotuner trial runs: step cap per instance (null otherwise)
     int write_back;          // 0: trial run, the caller's states are not touched
     double gamma, cfl, eps, c_lambda, C_thr, L_char;
     int alpha_thr, hybrid, bc_lo, bc_hi;
@@ -109,7 +111,8 @@ __global__ void __launch_bounds__(NT) k_batch(BatchArgs b)
         long long steps = 0;
         int status = 0;
         __syncthreads();
-        while (steps < b.max_steps) {
+        const long long max_steps = b.trial_caps != nullptr ? (long long)b.trial_caps[inst] : (long long)b.max_steps;
+        while (steps < max_steps) {
             // CFL max-reduction (same per-cell arithmetic as the grid solver)
             double smax = 0.0;
             bool bad = false;
@@ -218,6 +221,8 @@ struct weno_batch {
     double* t_out = nullptr;
     unsigned int* head = nullptr;
     unsigned long long* wcount = nullptr;
+    int* trial_caps = nullptr;
+    std::vector<int> n_host;
     int variant = 0;
     int blocks = 0;
     cudaGraphExec_t graph = nullptr;
@@ -302,11 +307,13 @@ static weno_status set_variant(weno_batch* bt, int v, int blocks_per_sm_cap)
 }
 
 // reset the queue and launch once (on stream s, optionally under capture)
-static cudaError_t enqueue_run(weno_batch* bt, void* U, int max_steps, int write_back, cudaStream_t s)
+static cudaError_t enqueue_run(weno_batch* bt, void* U, int max_steps, int write_back, cudaStream_t s,
+                               const int* trial_caps = nullptr)
 {
     cudaError_t e = cudaMemsetAsync(bt->head, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
     BatchArgs b = batch_args(bt, U, max_steps, write_back);
+    b.trial_caps = trial_caps;
     return batch_dispatch_launch(bt->prec, bt->variant, b, bt->blocks, s);
 }
 
@@ -314,7 +321,7 @@ static void batch_free(weno_batch* bt)
 {
     if (bt->graph) cudaGraphExecDestroy(bt->graph);
     void* ptrs[] = {bt->order, bt->n, bt->off, bt->goff, bt->dx, bt->t_end, bt->work[0], bt->work[1],
-                    bt->work[2], bt->status, bt->steps, bt->t_out, bt->head, bt->wcount};
+                    bt->work[2], bt->status, bt->steps, bt->t_out, bt->head, bt->wcount, bt->trial_caps};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (bt->cap) cudaStreamDestroy(bt->cap);
@@ -399,6 +406,8 @@ weno_status weno_batch_create(const weno_batch_desc* d, const weno_params* param
     alloc((void**)&bt->t_out, sizeof(double) * cnt);
     alloc((void**)&bt->head, sizeof(unsigned int));
     alloc((void**)&bt->wcount, sizeof(unsigned long long));
+    alloc((void**)&bt->trial_caps, sizeof(int) * cnt);
+    bt->n_host.assign(d->n, d->n + cnt);
     if (e == cudaSuccess) e = cudaMemcpy(bt->order, order.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(bt->n, d->n, sizeof(int) * cnt, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(bt->off, off.data(), sizeof(long long) * cnt, cudaMemcpyHostToDevice);
@@ -495,6 +504,14 @@ weno_status weno_batch_weno_face_count(weno_batch* bt, unsigned long long* count
 weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_steps, int* choice)
 {
     if (!bt || !U_dev || trial_steps < 1) return WENO_ERR_INVALID_ARG;
+    // trial steps per instance in proportion to its cells: a full run's step
+    // count grows with the cell count (the CFL step shrinks with dx), so its
+    // work grows like N^2, and the trial keeps that shape
+    const int nmax = *std::max_element(bt->n_host.begin(), bt->n_host.end());
+    std::vector<int> tc(bt->count);
+    for (int i = 0; i < bt->count; ++i)
+        tc[i] = std::max(1, (int)std::ceil((double)trial_steps * bt->n_host[i] / nmax));
+    BCK(cudaMemcpy(bt->trial_caps, tc.data(), sizeof(int) * bt->count, cudaMemcpyHostToDevice));
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
@@ -509,7 +526,7 @@ weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_ste
             float ms = 1e30f;
             for (int r = 0; r < 2; ++r) {   // first run loads the kernel
                 if (cudaEventRecord(e0, bt->stream) != cudaSuccess ||
-                    enqueue_run(bt, const_cast<void*>(U_dev), trial_steps, 0, bt->stream) != cudaSuccess ||
+                    enqueue_run(bt, const_cast<void*>(U_dev), trial_steps, 0, bt->stream, bt->trial_caps) != cudaSuccess ||
                     cudaEventRecord(e1, bt->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
                     bt->err = "batch autotune launch failed";
                     st = WENO_ERR_CUDA;
