@@ -45,10 +45,16 @@ FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA lanes per SM per clock on GB300
 FP32_FLOP_PER_CLK_SM = 256    # 128 FFMA lanes per SM per clock
 
 
+# sources of the sweep kernel that the committed ncu figures describe
+SWEEP_SOURCES = ("weno_device.cuh", "weno_kernels.cuh", "weno_launch.cuh", "weno_f64.cu", "weno_f32.cu")
+
+
 def csrc_digest() -> str:
+    """Digest of the sweep kernel's sources (profiles/traffic.json is used only
+    while it matches)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1908_02464_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in SWEEP_SOURCES:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
