@@ -183,20 +183,24 @@ static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* ou
         cudaError_t e = issue_lf(c, in, slot, c->tm, s);
         if (e != cudaSuccess) return e;
     }
-    for (int d = 0; d < c->dim; ++d) {
+    // directions from the last to x: the sweep that fuses the RK update (and
+    // reads the accumulator and the base state, and writes the new state)
+    // runs along x, where those accesses are contiguous rows
+    for (int i = 0; i < c->dim; ++i) {
+        const int d = c->dim - 1 - i;
         wis::SweepArgs a = sweep_args(c, d);
         a.U = in;
         a.tm = c->tm;
         a.stage = stage;
         a.alpha_g = c->alpha_g + slot * 9 + 3 * d;
-        if (d == c->dim - 1) {
+        if (d == 0) {
             a.mode = wis::MODE_COMBINE;
             a.Un = base;
             a.out = out;
             a.acc = c->dim > 1 ? c->acc : nullptr;
             set_rk(a, ra, rb);
         } else {
-            a.mode = d == 0 ? wis::MODE_ACC_SET : wis::MODE_ACC_ADD;
+            a.mode = i == 0 ? wis::MODE_ACC_SET : wis::MODE_ACC_ADD;
             a.acc = c->acc;
         }
         cudaError_t e = do_sweep(c, d, a, s);
@@ -526,25 +530,31 @@ static weno_status ensure_rhs_bufs(weno_ctx* ctx)
 static weno_status issue_rhs(weno_ctx* ctx, double t, uint8_t* flags)
 {
     if (ctx->p.splitting == wis::SPLIT_LF) CK(issue_lf(ctx, ctx->rhs_in, 3, nullptr, ctx->stream));
-    long long foff = 0;
-    for (int d = 0; d < ctx->dim; ++d) {
+    // flags of direction d start after the faces of the directions before it
+    long long foff[3] = {0, 0, 0};
+    for (int d = 1; d < ctx->dim; ++d) {
+        long long nf = 1;
+        for (int k = 0; k < 3; ++k) nf *= (k == d - 1) ? (long long)ctx->n[k] + 1 : ctx->n[k];
+        foff[d] = foff[d - 1] + nf;
+    }
+    // directions from the last to x, as in a step: the sweep that writes the
+    // result runs along x
+    for (int i = 0; i < ctx->dim; ++i) {
+        const int d = ctx->dim - 1 - i;
         wis::SweepArgs a = sweep_args(ctx, d);
         a.U = ctx->rhs_in;
         a.xs_fixed = wis::dmr_shock_x(t);
         a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
-        if (flags) a.flags = flags + foff;
-        if (d == ctx->dim - 1) {
+        if (flags) a.flags = flags + foff[d];
+        if (d == 0) {
             a.mode = wis::MODE_RHS;
             a.acc = ctx->dim > 1 ? ctx->acc : nullptr;
             a.out = ctx->rhs_out;
         } else {
-            a.mode = d == 0 ? wis::MODE_ACC_SET : wis::MODE_ACC_ADD;
+            a.mode = i == 0 ? wis::MODE_ACC_SET : wis::MODE_ACC_ADD;
             a.acc = ctx->acc;
         }
         CK(do_sweep(ctx, d, a, ctx->stream));
-        long long nf = 1;
-        for (int k = 0; k < 3; ++k) nf *= (k == d) ? (long long)ctx->n[k] + 1 : ctx->n[k];
-        foff += nf;
     }
     return WENO_OK;
 }
