@@ -260,15 +260,29 @@ weno_status weno_batch_run(weno_batch* batch, void* U_dev);
  * Synchronizes; returns WENO_ERR_NONPHYSICAL if any instance failed. */
 weno_status weno_batch_results(weno_batch* batch, int* status, long long* steps, double* t);
 
-/* Autotuner (no counterpart in the paper): times trial runs on U_dev (not
- * modified) for each CTA size (64, 128, 256 threads: tiles of 63, 127, 255
- * faces) and residency (all that fit, 4 or 2 CTAs per SM) and keeps the
- * fastest.  In a trial run instance i takes ceil(trial_steps N_i / N_max)
- * steps (at least one): a full run's step count grows with the cell count,
- * so the trial keeps the full run's work per instance, growing like N_i^2,
- * and with it the load balance of the schedule.  choice[0] = tile variant,
- * choice[1] = CTAs launched.  Synchronizes. */
+/* Autotuner (no counterpart in the paper): times trial runs for each CTA
+ * size (64, 128, 256 threads: tiles of 63, 127, 255 faces) and residency
+ * (all that fit, 4 or 2 CTAs per SM) and keeps the fastest.  U_dev is not
+ * modified.  The trials start from a scratch copy of U_dev advanced with
+ * the current configuration to half of each instance's end time: the cost
+ * of a step changes as the waves spread, and trials from the initial states
+ * rank the configurations unlike full runs do.  This pass costs about half
+ * a run and allocates the scratch state and a t_end array for the call.  In
+ * a trial run instance i takes ceil(trial_steps N_i / N_max) steps (at least
+ * one): a full run's step count grows with the cell count, so the trial
+ * keeps the full run's work per instance, growing like N_i^2, and with it
+ * the load balance of the schedule.  choice[0] = tile variant, choice[1] =
+ * CTAs launched.  The per-instance results afterwards are those of the last
+ * trial.  Synchronizes. */
 weno_status weno_batch_autotune(weno_batch* batch, const void* U_dev, int trial_steps, int* choice);
+
+/* Fixes the configuration without timing (no counterpart in the paper):
+ * variant 0, 1, 2 = 128-, 64-, 256-thread CTAs (tiles of 127, 63, 255
+ * faces); blocks_per_sm = resident CTAs per SM, 0 = as many as fit (values
+ * above that are lowered to it).  *blocks (may be NULL) receives the CTAs a
+ * run launches: min(count, residency x SMs).  WENO_ERR_INVALID_ARG for a
+ * variant outside 0..2 or a negative blocks_per_sm. */
+weno_status weno_batch_set_config(weno_batch* batch, int variant, int blocks_per_sm, int* blocks);
 
 /* Number of faces computed with the WENO (non-linear) flux by the batch's
  * runs (autotuner trial runs included) since creation or the last call with

@@ -501,6 +501,18 @@ weno_status weno_batch_weno_face_count(weno_batch* bt, unsigned long long* count
     return WENO_OK;
 }
 
+weno_status weno_batch_set_config(weno_batch* bt, int variant, int blocks_per_sm, int* blocks)
+{
+    if (!bt) return WENO_ERR_INVALID_ARG;
+    if (variant < 0 || variant >= wis::kBatchVariants || blocks_per_sm < 0) {
+        bt->err = "set_config: variant must be 0, 1 or 2 and blocks_per_sm >= 0";
+        return WENO_ERR_INVALID_ARG;
+    }
+    const weno_status st = set_variant(bt, variant, blocks_per_sm);
+    if (st == WENO_OK && blocks) *blocks = bt->blocks;
+    return st;
+}
+
 weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_steps, int* choice)
 {
     if (!bt || !U_dev || trial_steps < 1) return WENO_ERR_INVALID_ARG;
@@ -512,9 +524,44 @@ weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_ste
     for (int i = 0; i < bt->count; ++i)
         tc[i] = std::max(1, (int)std::ceil((double)trial_steps * bt->n_host[i] / nmax));
     BCK(cudaMemcpy(bt->trial_caps, tc.data(), sizeof(int) * bt->count, cudaMemcpyHostToDevice));
+    // the trials start from a scratch copy advanced to half of each
+    // instance's end time: the cost of a step depends on how far the waves
+    // have spread, and trials from the initial jumps rank the configurations
+    // unlike full runs do (they favour small tiles that lose on developed
+    // solutions)
+    const size_t sbytes = (size_t)bt->total_cells * 3 * bt->esz;
+    void* Us = nullptr;
+    double* t_half = nullptr;
+    BCK(cudaMalloc(&Us, sbytes));
+    if (cudaMalloc(&t_half, sizeof(double) * bt->count) != cudaSuccess) {
+        cudaFree(Us);
+        bt->err = "autotune: out of device memory";
+        return WENO_ERR_CUDA;
+    }
+    std::vector<double> th(bt->count);
+    cudaError_t ce = cudaMemcpy(th.data(), bt->t_end, sizeof(double) * bt->count, cudaMemcpyDeviceToHost);
+    for (double& x : th) x *= 0.5;
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(t_half, th.data(), sizeof(double) * bt->count, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(Us, U_dev, sbytes, cudaMemcpyDeviceToDevice, bt->stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(bt->head, 0, sizeof(unsigned int), bt->stream);
+    if (ce == cudaSuccess) {
+        BatchArgs b = batch_args(bt, Us, bt->max_steps, 1);
+        b.t_end = t_half;
+        ce = batch_dispatch_launch(bt->prec, bt->variant, b, bt->blocks, bt->stream);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(bt->stream);
+    cudaFree(t_half);
+    if (ce != cudaSuccess) {
+        cudaFree(Us);
+        bt->err = std::string("autotune: developing the trial state: ") + cudaGetErrorString(ce);
+        return WENO_ERR_CUDA;
+    }
     cudaEvent_t e0, e1;
-    BCK(cudaEventCreate(&e0));
-    BCK(cudaEventCreate(&e1));
+    if (cudaEventCreate(&e0) != cudaSuccess) { cudaFree(Us); bt->err = "cudaEventCreate"; return WENO_ERR_CUDA; }
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0); cudaFree(Us); bt->err = "cudaEventCreate"; return WENO_ERR_CUDA;
+    }
     float best = 1e30f;
     int best_v = bt->variant, best_cap = 0;
     const int caps[3] = {0, 4, 2};   // 0 = as many CTAs per SM as fit
@@ -526,7 +573,7 @@ weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_ste
             float ms = 1e30f;
             for (int r = 0; r < 2; ++r) {   // first run loads the kernel
                 if (cudaEventRecord(e0, bt->stream) != cudaSuccess ||
-                    enqueue_run(bt, const_cast<void*>(U_dev), trial_steps, 0, bt->stream, bt->trial_caps) != cudaSuccess ||
+                    enqueue_run(bt, Us, trial_steps, 0, bt->stream, bt->trial_caps) != cudaSuccess ||
                     cudaEventRecord(e1, bt->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
                     bt->err = "batch autotune launch failed";
                     st = WENO_ERR_CUDA;
@@ -539,6 +586,7 @@ weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_ste
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaFree(Us);
     if (st != WENO_OK) return st;
     st = set_variant(bt, best_v, best_cap);
     if (choice) { choice[0] = best_v; choice[1] = bt->blocks; }

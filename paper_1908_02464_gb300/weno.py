@@ -83,6 +83,7 @@ SIGNATURES = {
     "weno_batch_run": (ctypes.c_int, [_vp, _vp]),
     "weno_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(_ip), ctypes.POINTER(ctypes.c_longlong), _dp]),
     "weno_batch_weno_face_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong), _ip]),
+    "weno_batch_set_config": (ctypes.c_int, [_vp, _ip, _ip, ctypes.POINTER(ctypes.c_int)]),
     "weno_batch_autotune": (ctypes.c_int, [_vp, _vp, _ip, ctypes.POINTER(_ip)]),
     "weno_batch_destroy": (None, [_vp]),
     "weno_batch_last_error": (ctypes.c_char_p, [_vp]),
@@ -501,6 +502,13 @@ class Batch:
 
     def autotune(self, U_dev, trial_steps: int = 4):
         return weno_batch_autotune(self.handle, U_dev, trial_steps)
+
+    def set_config(self, variant: int, blocks_per_sm: int = 0) -> int:
+        """Fix the tile variant and residency without timing; returns the CTAs a run launches."""
+        b = ctypes.c_int(0)
+        _bcheck(load().weno_batch_set_config(self.handle, int(variant), int(blocks_per_sm), ctypes.byref(b)),
+                self.handle)
+        return b.value
 
     def weno_faces(self, reset: bool = False) -> int:
         c = ctypes.c_ulonglong(0)

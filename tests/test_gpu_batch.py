@@ -120,6 +120,33 @@ def test_batch_autotune_keeps_input_and_results():
     ref.close()
 
 
+def test_batch_set_config_every_tile_and_residency_gives_the_same_states():
+    # one CTA integrates one instance, and the face fluxes and the CFL maximum
+    # do not depend on how the faces are cut into tiles, so every fixed
+    # configuration gives the same bits
+    params, states = _small_batch(count=24, seed=5)
+    b = weno.Batch(params["N"], 0.0, 1.0, params["t_end"], "fp64")
+    ref = None
+    for v in range(3):
+        for cap in (0, 2, 1):
+            blocks = b.set_config(v, cap)
+            assert 1 <= blocks <= len(states)
+            if cap == 1:
+                assert blocks == min(len(states), torch.cuda.get_device_properties(0).multi_processor_count)
+            U = b.pack(states)
+            b.run(U)
+            st, steps, t = b.results()
+            if ref is None:
+                ref = (U.clone(), st.copy(), steps.copy())
+            else:
+                assert torch.equal(U, ref[0]), (v, cap)
+                assert np.array_equal(st, ref[1]) and np.array_equal(steps, ref[2]), (v, cap)
+    for bad in ((3, 0), (-1, 0), (0, -1)):
+        with pytest.raises(RuntimeError):
+            b.set_config(*bad)
+    b.close()
+
+
 def test_batch_replay_and_one_call_form():
     params, states = _small_batch(count=10, seed=8)
     b = weno.Batch(params["N"], 0.0, 1.0, params["t_end"], "fp64")
