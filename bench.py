@@ -553,12 +553,48 @@ def host_info() -> dict:
     return {"host_cores": os.cpu_count(), "cpu_model": model or platform.machine()}
 
 
+def oracle_worker(steps: int) -> None:
+    """One single-threaded oracle process of the all-core baseline: prints
+    the wall-clock start and end of its timed steps as one JSON line."""
+    from oracle import oracle as orc
+    from paper_1908_02464_gb300 import problems as P
+    prob, U = P.double_mach(NX, NY)
+    t0 = time.time()
+    t = 0.0
+    for _ in range(steps):
+        st, t, dt = orc.step(prob, U, t, 1.0)
+    print(json.dumps({"start": t0, "end": time.time()}), flush=True)
+
+
+def cpu_all_cores(steps: int) -> dict:
+    """The unmodified single-threaded oracle run as one process per host
+    core, all at once, each on its own copy of the workload; throughput =
+    all processes' cell-updates / (last end - first start)."""
+    n = os.cpu_count() or 1
+    cmd = [sys.executable, "-c", f"import bench; bench.oracle_worker({int(steps)})"]
+    procs = [subprocess.Popen(cmd, cwd=ROOT, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+             for _ in range(n)]
+    spans = []
+    for p in procs:
+        out, _ = p.communicate()
+        if p.returncode == 0 and out.strip():
+            spans.append(json.loads(out.strip().splitlines()[-1]))
+    if len(spans) != n:
+        return {"unavailable": f"{n - len(spans)} of {n} oracle processes failed"}
+    wall = max(x["end"] for x in spans) - min(x["start"] for x in spans)
+    return {"value": 3.0 * NX * NY * steps * n / wall, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} concurrent single-threaded oracle processes, each {steps} FP64 RK3 steps of the "
+                      f"{NX}x{NY} double Mach reflection from its initial condition ({wall:.1f} s wall)"}
+
+
 def cpu_baseline(args) -> dict:
     steps = args.cpu_steps
     el, _, _ = oracle_steps(steps)
-    return {"value": 3.0 * NX * NY * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} FP64 RK3 steps of the {NX}x{NY} double Mach reflection from its initial "
-                      f"condition, single-threaded C++ oracle ({el:.1f} s)", **host_info()}
+    out = {"value": 3.0 * NX * NY * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{steps} FP64 RK3 steps of the {NX}x{NY} double Mach reflection from its initial "
+                     f"condition, single-threaded C++ oracle ({el:.1f} s)", **host_info()}
+    out["all_cores"] = cpu_all_cores(max(1, steps // 4))
+    return out
 
 
 def run_reference(args) -> dict | None:
