@@ -223,13 +223,12 @@ static cudaError_t issue_step(weno_ctx* c, int ph, cudaStream_t s)
     ca.tm = c->tm;
     cudaError_t e = do_cfl(c, ca, s);
     if (e != cudaSuccess) return e;
-    wis::k_dt<<<1, 1, 0, s>>>(c->tm, c->p.cfl, c->smax_floor);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = wis::launch_pdl(wis::k_dt, dim3(1), dim3(1), 0, s, c->tm, c->p.cfl, c->smax_floor);
+    if (e != cudaSuccess) return e;
     if ((e = issue_stage(c, cur, nullptr, x, 0.0, 1.0, 0, 0, s)) != cudaSuccess) return e;
     if ((e = issue_stage(c, x, cur, y, 0.75, 0.25, 1, 1, s)) != cudaSuccess) return e;
     if ((e = issue_stage(c, y, cur, x, 1.0 / 3.0, 2.0 / 3.0, 2, 2, s)) != cudaSuccess) return e;
-    wis::k_post<<<1, 1, 0, s>>>(c->tm);
-    return cudaGetLastError();
+    return wis::launch_pdl(wis::k_post, dim3(1), dim3(1), 0, s, c->tm);
 }
 
 static weno_status build_graphs(weno_ctx* ctx)

@@ -25,6 +25,36 @@
 
 namespace wis {
 
+// Programmatic dependent launch.  The kernels of a time step are launched
+// with programmatic stream serialization (launch_pdl), so that a kernel's
+// CTAs can become resident while its predecessor's last wave finishes.
+// Every such kernel calls pdl_enter before its first access to global
+// memory: griddepcontrol.wait returns once the predecessor grid has
+// completed and its writes are visible (at once for an ordinary launch),
+// and launch_dependents then lets the successor launch.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              A&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 // Device-resident time state of a context.
 struct DevTime {
     double t;                       // time of the current state
@@ -621,6 +651,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
 template <typename T, int DIM, int DIR, int LINES, int SEG, int NT, bool EXACTDET, bool FLAT = false>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
 {
+    pdl_enter();
     if (a.tm != nullptr) {
         if (a.tm->status != 0 || !(a.tm->dt > 0.0)) return;
     }
@@ -773,6 +804,7 @@ __device__ __forceinline__ double cfl_step(double cfl, double smax, double t, do
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_cfl(CflArgs a)
 {
+    pdl_enter();
     constexpr int NV = DIM + 2;
     if (a.tm->status != 0) return;
     const T* U = reinterpret_cast<const T*>(a.U);
@@ -823,6 +855,7 @@ __global__ void __launch_bounds__(256) k_cfl(CflArgs a)
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_lf_alpha(CflArgs a, unsigned long long* out)
 {
+    pdl_enter();
     constexpr int NV = DIM + 2;
     if (a.tm != nullptr && (a.tm->status != 0 || !(a.tm->dt > 0.0))) return;
     const T* U = reinterpret_cast<const T*>(a.U);
@@ -867,6 +900,7 @@ __global__ void __launch_bounds__(256) k_lf_alpha(CflArgs a, unsigned long long*
 // domain through the ghost cells)
 static __global__ void k_dt(DevTime* tm, double cfl, double smax_floor)
 {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double dt = 0.0;
     int clipped = 0;
@@ -891,6 +925,7 @@ static __global__ void k_set_tend(DevTime* tm, double t_end)
 
 static __global__ void k_post(DevTime* tm)
 {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (tm->status == 0 && tm->dt > 0.0) {
         tm->t = tm->clipped ? tm->t_end : tm->t + tm->dt;

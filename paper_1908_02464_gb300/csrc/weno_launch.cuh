@@ -61,8 +61,7 @@ cudaError_t launch_sweep_one(const SweepArgs& a, cudaStream_t s)
     } else if (DIR == 0) grid = dim3(segs, (a.n[1] + TL::LINES - 1) / TL::LINES, a.n[2]);
     else if (DIR == 1) grid = dim3((a.n[0] + TL::LINES - 1) / TL::LINES, segs, a.n[2]);
     else grid = dim3((a.n[0] + TL::LINES - 1) / TL::LINES, a.n[1], segs);
-    kern<<<grid, TL::NT, SM::bytes, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, dim3(TL::NT), SM::bytes, s, a);
 }
 
 template <typename T, int DIM, int DIR, bool EXACTDET>
@@ -127,10 +126,9 @@ cudaError_t launch_cfl_t(int dim, const CflArgs& a_in, int nsm, cudaStream_t s)
     if (parts < 1) parts = 1;
     a.parts = (int)parts;
     const int blocks = grid_for(rows * parts * 256, 256, nsm * 8);
-    if (dim == 1) k_cfl<T, 1><<<blocks, 256, 0, s>>>(a);
-    else if (dim == 2) k_cfl<T, 2><<<blocks, 256, 0, s>>>(a);
-    else k_cfl<T, 3><<<blocks, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    if (dim == 1) return launch_pdl(k_cfl<T, 1>, dim3(blocks), dim3(256), 0, s, a);
+    if (dim == 2) return launch_pdl(k_cfl<T, 2>, dim3(blocks), dim3(256), 0, s, a);
+    return launch_pdl(k_cfl<T, 3>, dim3(blocks), dim3(256), 0, s, a);
 }
 
 template <typename T>
@@ -138,10 +136,9 @@ cudaError_t launch_lf_t(int dim, const CflArgs& a, unsigned long long* out, int 
 {
     const long long cells = (long long)a.n[0] * a.n[1] * a.n[2];
     const int blocks = grid_for(cells, 256, nsm * 8);
-    if (dim == 1) k_lf_alpha<T, 1><<<blocks, 256, 0, s>>>(a, out);
-    else if (dim == 2) k_lf_alpha<T, 2><<<blocks, 256, 0, s>>>(a, out);
-    else k_lf_alpha<T, 3><<<blocks, 256, 0, s>>>(a, out);
-    return cudaGetLastError();
+    if (dim == 1) return launch_pdl(k_lf_alpha<T, 1>, dim3(blocks), dim3(256), 0, s, a, out);
+    if (dim == 2) return launch_pdl(k_lf_alpha<T, 2>, dim3(blocks), dim3(256), 0, s, a, out);
+    return launch_pdl(k_lf_alpha<T, 3>, dim3(blocks), dim3(256), 0, s, a, out);
 }
 
 template <typename T>
