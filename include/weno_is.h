@@ -200,9 +200,9 @@ weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t fl
 /* Tile autotuner (no counterpart in the paper): for every sweep direction,
  * times each compiled tile shape `reps` times on the current state and keeps
  * the fastest for this context.  Shapes (variant: lines x cells per CTA):
- * 0: 2x63, 1: 8x15, 2: 4x31, 3: 1x127, 4: 1x95, 5: flat, 128 consecutive
+ * 0: 2x63, 1: 8x15, 2: 4x31, 3: 1x127, 4: 1x95, 5: flat, 123 consecutive
  * faces of the line-after-line face sequence (a tile may end one line and
- * start the next; lines shorter than 127 cells take variant 3).  Defaults:
+ * start the next; lines shorter than 122 cells take variant 3).  Defaults:
  * FP64 5 in every direction; FP32 and mixed 3 along x, 1 across.
  * variants[3] (if not NULL) receives the choice per direction.
  * The state is not changed; the step graphs are rebuilt on next use.

@@ -1,7 +1,7 @@
 // Kernels of the regularized WENO-IS Euler solver (sm_103a).
 //
 //   k_sweep   one direction of the semi-discrete operator (Eq. goveq5): a
-//             tile of LINES grid lines x SEG cells along the sweep (or 128
+//             tile of LINES grid lines x SEG cells along the sweep (or 123
 //             consecutive faces of the line-after-line face sequence),
 //             staged in shared memory with a 3-cell halo whose ghost cells
 //             come from the boundary conditions; every face of the tile goes

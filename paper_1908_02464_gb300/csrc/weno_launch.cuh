@@ -22,10 +22,12 @@ namespace wis {
 // rows.  weno_autotune times the variants on a live state and keeps the best.
 //   3 single  1 x 127 halo work ~5%
 //   4 small   1 x 95  96-thread CTAs (more resident CTAs per SM)
-//   5 flat    128 consecutive faces of the line-after-line face sequence: no
+//   5 flat    123 consecutive faces of the line-after-line face sequence: no
 //             partly filled tile at the end of each line (512 cells = 4 x 127
-//             + 4 leaves a 4-cell tile per line otherwise); lines shorter
-//             than 127 cells take variant 3 instead
+//             + 4 leaves a 4-cell tile per line otherwise), and a tile within
+//             one line stages exactly 128 cells, one per thread, where 128
+//             faces would leave a second round of 5 cells; lines shorter
+//             than 122 cells take variant 3 instead
 constexpr int kTileVariants = 6;
 template <int V> struct Tile;
 template <> struct Tile<0> { static constexpr int LINES = 2, SEG = 63, NT = 128; static constexpr bool FLAT = false; };
@@ -33,7 +35,7 @@ template <> struct Tile<1> { static constexpr int LINES = 8, SEG = 15, NT = 128;
 template <> struct Tile<2> { static constexpr int LINES = 4, SEG = 31, NT = 128; static constexpr bool FLAT = false; };
 template <> struct Tile<3> { static constexpr int LINES = 1, SEG = 127, NT = 128; static constexpr bool FLAT = false; };
 template <> struct Tile<4> { static constexpr int LINES = 1, SEG = 95, NT = 96; static constexpr bool FLAT = false; };
-template <> struct Tile<5> { static constexpr int LINES = 1, SEG = 127, NT = 128; static constexpr bool FLAT = true; };
+template <> struct Tile<5> { static constexpr int LINES = 1, SEG = 122, NT = 128; static constexpr bool FLAT = true; };
 struct Tile1D { static constexpr int LINES = 1, SEG = 127, NT = 128; static constexpr bool FLAT = false; };
 
 template <typename T, int DIM, int DIR, bool EXACTDET, typename TL>
