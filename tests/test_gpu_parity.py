@@ -387,7 +387,9 @@ def test_step_equals_advance_bitwise():
 
 def _variant_cases():
     cases = []
-    for dim, n in ((2, [150, 37]), (2, [300, 140]), (3, [40, 23, 19]), (3, [130, 9, 128])):
+    # 122 cells: the shortest lines that take flat tiles, so that a tile
+    # starting late in one line covers the whole of the next line's start
+    for dim, n in ((2, [150, 37]), (2, [300, 140]), (2, [122, 121]), (3, [40, 23, 19]), (3, [130, 9, 128])):
         cases.append(P.random_state(dim, n, seed=77, kind="mixed"))
     # non-periodic boundaries on lines long enough for flat tiles: double Mach
     # (inflow, wall, moving shock), the jet inflow, and a 3D box with
@@ -418,7 +420,7 @@ def test_rhs_parity_3d_walls_flat_tiles():
 def test_tile_variants_give_bitwise_identical_results(precision):
     """Every face is computed by the same arithmetic whatever the tiling,
     including flat tiles (variant 5) whose pieces span two lines, and the
-    fallback to variant 3 on lines shorter than 127 cells."""
+    fallback to variant 3 on lines shorter than 122 cells."""
     for prob, U in _variant_cases():
         if precision != "fp64" and prob["name"] == "mach2000_jet":
             continue   # FP32 cannot represent the jet's pressure (see the jet tests)
