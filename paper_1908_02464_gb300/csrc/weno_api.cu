@@ -800,7 +800,7 @@ weno_status weno_autotune(weno_ctx* ctx, int reps, int* variants)
                 ctx->tile[d] = v;
                 double m = 0.0;
                 st = time_sweep_dir(ctx, d, 1, nullptr, 0, e0, e1, &m, nullptr);
-                if (r > 0 && m < best_ms[v]) best_ms[v] = m;   // round 0 warms up
+                if (r > 0 && m < best_ms[v]) best_ms[v] = m;   // the first repetition warms up
             }
         }
         int best = keep;
