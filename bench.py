@@ -310,6 +310,7 @@ def run_ours(args) -> dict:
     vortex = None if args.no_vortex else vortex3d_rhs_vjp(args)
     jet = None if args.no_jet else mach2000_jet_run(args)
     shu = None if args.no_shu else shu_osher_precisions(args)
+    thr = None if args.no_shu else threshold_study(args)
 
     launches_per_step = 3 + 3 * 2 + 1   # cfl, dt, post, 3 stages x 2 sweeps, set_tend
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -332,6 +333,8 @@ def run_ours(args) -> dict:
         res["mach2000_jet"] = jet
     if shu is not None:
         res["shu_osher_400"] = shu
+    if thr is not None:
+        res["threshold_study_shu_osher_400"] = thr
     if rank == 0 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args)
     if ws > 1:
@@ -419,6 +422,43 @@ def shu_osher_precisions(args) -> dict:
         r = V[0].astype(np.float64)
         out[prec] = {"l1_rho": float(np.mean(np.abs(r - ref))), "linf_rho": float(np.max(np.abs(r - ref))),
                      "steps": k, "wall_s": wall, "cell_updates_per_s": 3.0 * 400 * k / wall}
+    return out
+
+
+def threshold_study(args) -> dict:
+    """The switch threshold eps_h = C (dx / L)^3 of Sec. 3 against accuracy:
+    Shu-Osher at 400 cells to t = 1.8 in FP64 for several characteristic
+    lengths L, with the per-face and the per-field hybrid and with the hybrid
+    off.  Per run: the fraction of faces that took the WENO flux (the
+    solver's own counter), L1 / Linf of density against the oracle's
+    3200-cell solution, steps and wall time."""
+    import torch
+    from paper_1908_02464_gb300 import problems as P
+    from paper_1908_02464_gb300 import weno
+    path = os.path.join(ROOT, "tests", "golden", "shu_osher_rho_ref400.txt")
+    ref = np.array([float(l) for l in open(path) if not l.startswith("#")])
+    runs = [(0, 1.0)] + [(h, L) for h in (1, 2) for L in (0.25, 0.5, 1.0, 2.0, 4.0, 8.0)]
+    out = {"cells": 400, "t_end": 1.8, "precision": "fp64", "C_thr": 1.0, "alpha_thr": 3,
+           "hybrid_modes": {"0": "off (WENO everywhere)", "1": "per face", "2": "per field"}, "runs": []}
+    for hybrid, L in runs:
+        prob, U = P.shu_osher(400)
+        prob["hybrid"] = hybrid
+        prob["L_char"] = L
+        s = weno.Solver(prob, "fp64")
+        s.set_state(U)
+        s.weno_faces(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = s.advance(prob["t_end"])
+        wall = time.perf_counter() - t0
+        wf = s.weno_faces()
+        V, _ = s.get_state()
+        s.close()
+        r = V[0].astype(np.float64)
+        out["runs"].append({"hybrid": hybrid, "L_char": L, "steps": k,
+                            "weno_face_fraction": wf / (3.0 * 401 * k),
+                            "l1_rho": float(np.mean(np.abs(r - ref))), "linf_rho": float(np.max(np.abs(r - ref))),
+                            "wall_s": wall})
     return out
 
 

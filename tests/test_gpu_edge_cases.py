@@ -114,3 +114,35 @@ def test_large_3d_grid_sampled_against_oracle():
         kappa = np.maximum(kappa, np.max(np.abs(_oracle_rhs_at(prob, U, cells, prng) - ref), axis=0))
     scale = np.max(np.abs(r).reshape(5, -1), axis=1)
     assert np.all(np.max(np.abs(got - ref), axis=0) <= np.maximum(1e-12 * scale, 10.0 * kappa))
+
+
+def test_switch_threshold_flags_are_nested_in_the_characteristic_length():
+    """eps_h = C (dx / L)^3 (Sec. 3) falls as L grows, so on fixed data every
+    face that takes the WENO flux at L still takes it at 2 L, and at least as
+    many faces do; the flags at L = 1 are the oracle's."""
+    prob, U0 = P.shu_osher(400)
+    s = weno.Solver(prob, "fp64")
+    s.set_state(U0)
+    s.advance(prob["t_end"])          # the developed shock / entropy-wave field
+    U, _ = s.get_state()
+    s.close()
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    Ud = torch.from_numpy(U).cuda()
+    prev = None
+    counts = []
+    for L in (0.25, 0.5, 1.0, 2.0, 4.0, 8.0):
+        pr = dict(prob)
+        pr["L_char"] = L
+        s = weno.Solver(pr, "fp64")
+        flags = s.face_flags(Ud).cpu().numpy()
+        s.close()
+        weno_faces = flags == 0
+        if prev is not None:
+            assert np.all(weno_faces[prev]), L
+        prev = weno_faces
+        counts.append(int(weno_faces.sum()))
+        if L == 1.0:
+            _, oflags, ratio = orc.rhs(prob, U, 0.0, want_flags=True)
+            mism = np.nonzero(flags != oflags)[0]
+            assert np.all(np.abs(ratio[mism] - 1.0) < 1e-9), len(mism)
+    assert counts[-1] > counts[0], counts
