@@ -18,8 +18,10 @@
 // smooth and this is the derivative of the active piece.
 //
 // Accumulation is deterministic: a tile of SEG cells recomputes the SEG + 5
-// faces that touch its cells, writes each face's contribution to the six
-// stencil-cell records in shared memory, and gathers them per cell.
+// faces that touch its cells, writes each face's contribution to its six
+// stencil cells in shared memory (U and F bars for all six, Roe-field bars
+// for the two neighbours, one bar per LLF speed for the cell attaining it),
+// and gathers them per cell in face order.
 // Contributions to ghost cells go to a per-line buffer that a second kernel
 // maps back through the boundary conditions.
 #pragma once
@@ -160,7 +162,9 @@ __device__ __forceinline__ void back_proj_adj(const Roe<T, DIM>& r, const T* w, 
     wb[LAST] += oE * r.H + sumb + difb;
 }
 
-// adjoint of the Roe average; gab/gbb: record bars of cells j and j+1
+// adjoint of the Roe average; gab/gbb: bars of the Roe fields of cells j and
+// j+1, relative to CL::SU (sqrt(rho) u at 0 .. DIM-1, sqrt(rho) H at DIM,
+// sqrt(rho) at DIM + 1)
 template <typename T, int DIM, typename GA, typename GB>
 __device__ __forceinline__ void roe_adj(GA get_a, GB get_b, T gamma, const Roe<T, DIM>& r, RoeBar<T, DIM> rb,
                                         T* gab, T* gbb)
@@ -179,16 +183,16 @@ __device__ __forceinline__ void roe_adj(GA get_a, GB get_b, T gamma, const Roe<T
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         const T ub = rb.u[k] + r.u[k] * rb.hq2;
-        gab[CL::SU + k] += ub * inv;
-        gbb[CL::SU + k] += ub * inv;
+        gab[k] += ub * inv;
+        gbb[k] += ub * inv;
         invb += ub * (get_a(CL::SU + k) + get_b(CL::SU + k));
     }
-    gab[CL::SH] += rb.H * inv;
-    gbb[CL::SH] += rb.H * inv;
+    gab[DIM] += rb.H * inv;
+    gbb[DIM] += rb.H * inv;
     invb += rb.H * (get_a(CL::SH) + get_b(CL::SH));
     const T sb_ = -invb * inv * inv;
-    gab[CL::SQ] += sb_ + rb.rt * sb;
-    gbb[CL::SQ] += sb_ + rb.rt * sa;
+    gab[DIM + 1] += sb_ + rb.rt * sb;
+    gbb[DIM + 1] += sb_ + rb.rt * sa;
 }
 
 // adjoint of the reconstruction: fb -> bars of a..e (accumulated) and of lam
@@ -287,7 +291,14 @@ struct VjpSmem {
     static constexpr int NC = SEG + 10;         // cells c0-5 .. c0+SEG+4
     static constexpr int NQ = CellLayout<DIM>::NQ;
     static constexpr int NV = DIM + 2;
-    static constexpr size_t bytes = sizeof(T) * ((size_t)NQ * NC + (size_t)NV * NC + (size_t)NF * 6 * NQ);
+    // per face: U and F bars of the six stencil cells, Roe-field bars of
+    // cells 2 and 3 (the face's neighbours), the three LLF speed bars, and
+    // (as one int) the stencil slots of the cells attaining the speeds
+    static constexpr int NUF = 2 * NV;
+    static constexpr int NRB = DIM + 2;
+    static constexpr int NFB = 6 * NUF + 2 * NRB + 3;
+    static constexpr size_t bytes =
+        sizeof(T) * ((size_t)NQ * NC + (size_t)NV * NC + (size_t)NF * NFB) + sizeof(int) * (size_t)NF;
 };
 
 // one direction of the VJP: tile = one grid line segment of SEG cells
@@ -298,10 +309,14 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
     using SM = VjpSmem<T, DIM>;
     constexpr int NV = DIM + 2, NQ = CL::NQ, SEG = SM::SEG, NF = SM::NF, NC = SM::NC;
     constexpr int NT = VjpTile<DIM>::NT;
+    constexpr int NUF = SM::NUF, NRB = SM::NRB, NFB = SM::NFB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ][NC]
     T* wq = cq + NQ * NC;                     // [NV][NC] cotangent
-    T* G = wq + NV * NC;                      // [NF][6][NQ] record bars per face
+    T* UF = wq + NV * NC;                     // [NF][6][NUF] U and F bars of the stencil cells
+    T* RB = UF + NF * 6 * NUF;                // [NF][2][NRB] Roe-field bars of cells 2 and 3
+    T* SP = RB + NF * 2 * NRB;                // [NF][3]      LLF speed bars
+    int* SL = reinterpret_cast<int*>(SP + NF * 3);   // [NF] slots attaining the speeds
 
     const int nd = a.n[DIR];
     const int c0 = blockIdx.x * SEG;
@@ -333,7 +348,7 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
             for (int v = 0; v < NV; ++v) wq[v * NC + p] = T(0);
         }
     }
-    for (int idx = threadIdx.x; idx < NF * 6 * NQ; idx += NT) G[idx] = T(0);
+    for (int idx = threadIdx.x; idx < NF * NFB; idx += NT) UF[idx] = T(0);
     __syncthreads();
 
     // ---- per face: forward recompute and reverse -------------------------
@@ -345,7 +360,8 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
         if (face < 0 || face > nd) continue;
         const int p0 = f;                       // tile index of stencil cell j-2 = face-3
         auto rec = [&](int m, int kk) -> T { return cq[kk * NC + p0 + m]; };
-        T* Gf = G + (size_t)f * 6 * NQ;         // bars of the six stencil cells
+        T* UFf = UF + (size_t)f * 6 * NUF;     // U and F bars of the six stencil cells
+        T* RBf = RB + (size_t)f * 2 * NRB;     // Roe-field bars of cells 2 and 3
         // cotangent of the face flux: (w_{right} - w_{left}) / dx
         T phi[NV];
 #pragma unroll
@@ -390,7 +406,7 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
 #pragma unroll
             for (int m = 0; m < 6; ++m)
 #pragma unroll
-                for (int v = 0; v < NV; ++v) Gf[m * NQ + CL::F + v] += cf[m] * Fb[v];
+                for (int v = 0; v < NV; ++v) UFf[m * NUF + CL::F + v] += cf[m] * Fb[v];
             T aw[NV], awb[NV];
             aw[0] = am * w[0];
 #pragma unroll
@@ -482,8 +498,8 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
                 proj_all_adj<T, DIM, DIR>(r, xf, gbar[m], xfb, rb);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    Gf[m * NQ + CL::U + v] += xub[v];
-                    Gf[m * NQ + CL::F + v] += xfb[v];
+                    UFf[m * NUF + CL::U + v] += xub[v];
+                    UFf[m * NUF + CL::F + v] += xfb[v];
                 }
             }
         }
@@ -496,11 +512,12 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
 #pragma unroll
         for (int m = 0; m < 6; ++m)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Gf[m * NQ + CL::U + v] += cd[m] * dUb[v];
-        Gf[im * NQ + CL::LM] += alb_m;
-        Gf[i0 * NQ + CL::L0] += alb_0;
-        Gf[ip * NQ + CL::LP] += alb_p;
-        roe_adj<T, DIM>(ga, gb, gamma, r, rb, Gf + 2 * NQ, Gf + 3 * NQ);
+            for (int v = 0; v < NV; ++v) UFf[m * NUF + CL::U + v] += cd[m] * dUb[v];
+        SP[f * 3 + 0] += alb_m;
+        SP[f * 3 + 1] += alb_0;
+        SP[f * 3 + 2] += alb_p;
+        SL[f] = im | (i0 << 4) | (ip << 8);
+        roe_adj<T, DIM>(ga, gb, gamma, r, rb, RBf, RBf + NRB);
     }
     __syncthreads();
 
@@ -522,9 +539,20 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
             const int f = fi - (c0 - 2);
             if (f < 0 || f >= NF) continue;
             const int m = cell - fi + 3;
-            const T* src = G + ((size_t)f * 6 + m) * NQ;
+            // the entries this cell receives from face fi, in the record
+            // layout; the others are zero for it
+            const T* uf = UF + ((size_t)f * 6 + m) * NUF;
 #pragma unroll
-            for (int kk = 0; kk < NQ; ++kk) qb[kk] += src[kk];
+            for (int kk = 0; kk < NUF; ++kk) qb[kk] += uf[kk];
+            if (m == 2 || m == 3) {
+                const T* rbp = RB + ((size_t)f * 2 + (m - 2)) * NRB;
+#pragma unroll
+                for (int kk = 0; kk < NRB; ++kk) qb[CL::SU + kk] += rbp[kk];
+            }
+            const int sl = SL[f];
+            if ((sl & 15) == m) qb[CL::LM] += SP[f * 3 + 0];
+            if (((sl >> 4) & 15) == m) qb[CL::L0] += SP[f * 3 + 1];
+            if (((sl >> 8) & 15) == m) qb[CL::LP] += SP[f * 3 + 2];
         }
         const int pc = cell - (c0 - 5);
         T U[NV], Ub[NV];
