@@ -282,13 +282,24 @@ struct VjpArgs {
     int hybrid;
 };
 
-template <int DIM> struct VjpTile { static constexpr int SEG = 59, NT = 64; };
+// A tile is LINES grid lines x SEG cells along the sweep, one thread per
+// face.  Lines along x take one line of 59 cells.  For y and z lines in FP32
+// a tile takes 8 x-adjacent lines of 27 cells, so that the strided loads of
+// one line position cover a 32-byte sector; in FP64 the arithmetic bounds
+// those sweeps and one line per tile keeps 4 CTAs per SM resident.
+template <typename T, int DIM, int DIR> struct VjpTile {
+    static constexpr int LINES = (DIR != 0 && sizeof(T) == 4) ? 8 : 1;
+    static constexpr int SEG = LINES == 1 ? 59 : 27;
+    static constexpr int NT = LINES * (SEG + 5);
+};
 
-template <typename T, int DIM>
+template <typename T, int DIM, int DIR>
 struct VjpSmem {
-    static constexpr int SEG = VjpTile<DIM>::SEG;
-    static constexpr int NF = SEG + 5;          // faces c0-2 .. c0+SEG+2
-    static constexpr int NC = SEG + 10;         // cells c0-5 .. c0+SEG+4
+    static constexpr int LINES = VjpTile<T, DIM, DIR>::LINES;
+    static constexpr int SEG = VjpTile<T, DIM, DIR>::SEG;
+    static constexpr int NF = SEG + 5;          // faces c0-2 .. c0+SEG+2 per line
+    static constexpr int NC = SEG + 10;         // cells c0-5 .. c0+SEG+4 per line
+    static constexpr int LNF = LINES * NF, LNC = LINES * NC;
     static constexpr int NQ = CellLayout<DIM>::NQ;
     static constexpr int NV = DIM + 2;
     // per face: U and F bars of the six stencil cells, Roe-field bars of
@@ -298,74 +309,81 @@ struct VjpSmem {
     static constexpr int NRB = DIM + 2;
     static constexpr int NFB = 6 * NUF + 2 * NRB + 3;
     static constexpr size_t bytes =
-        sizeof(T) * ((size_t)NQ * NC + (size_t)NV * NC + (size_t)NF * NFB) + sizeof(int) * (size_t)NF;
+        sizeof(T) * ((size_t)NQ * LNC + (size_t)NV * LNC + (size_t)LNF * NFB) + sizeof(int) * (size_t)LNF;
 };
 
-// one direction of the VJP: tile = one grid line segment of SEG cells
+// one direction of the VJP: tile = LINES grid lines x SEG cells; shared
+// arrays hold position p of line l at p * LINES + l
 template <typename T, int DIM, int DIR>
-__global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
+__global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT) k_vjp(VjpArgs a)
 {
     using CL = CellLayout<DIM>;
-    using SM = VjpSmem<T, DIM>;
-    constexpr int NV = DIM + 2, NQ = CL::NQ, SEG = SM::SEG, NF = SM::NF, NC = SM::NC;
-    constexpr int NT = VjpTile<DIM>::NT;
+    using SM = VjpSmem<T, DIM, DIR>;
+    constexpr int NV = DIM + 2, NQ = CL::NQ, SEG = SM::SEG, NF = SM::NF;
+    constexpr int LINES = SM::LINES, LNF = SM::LNF, LNC = SM::LNC;
+    constexpr int NT = VjpTile<T, DIM, DIR>::NT;
     constexpr int NUF = SM::NUF, NRB = SM::NRB, NFB = SM::NFB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ][NC]
-    T* wq = cq + NQ * NC;                     // [NV][NC] cotangent
-    T* UF = wq + NV * NC;                     // [NF][6][NUF] U and F bars of the stencil cells
-    T* RB = UF + NF * 6 * NUF;                // [NF][2][NRB] Roe-field bars of cells 2 and 3
-    T* SP = RB + NF * 2 * NRB;                // [NF][3]      LLF speed bars
-    int* SL = reinterpret_cast<int*>(SP + NF * 3);   // [NF] slots attaining the speeds
+    T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ][NC][LINES] cell records
+    T* wq = cq + NQ * LNC;                    // [NV][NC][LINES] cotangent
+    T* UF = wq + NV * LNC;                    // [NF][LINES][6][NUF] U and F bars of the stencil cells
+    T* RB = UF + LNF * 6 * NUF;               // [NF][LINES][2][NRB] Roe-field bars of cells 2 and 3
+    T* SP = RB + LNF * 2 * NRB;               // [NF][LINES][3] LLF speed bars
+    int* SL = reinterpret_cast<int*>(SP + LNF * 3);   // [NF][LINES] slots attaining the speeds
 
     const int nd = a.n[DIR];
     const int c0 = blockIdx.x * SEG;
-    // line coordinates: the two indices other than DIR
-    int i = 0, j = 0, k = 0;
+    // line coordinates: the two indices other than DIR; the lines of a
+    // multi-line tile are consecutive in x
+    int ix0 = 0, j = 0, k = 0;
     if (DIR == 0) { j = blockIdx.y; k = blockIdx.z; }
-    else if (DIR == 1) { i = blockIdx.y; k = blockIdx.z; }
-    else { i = blockIdx.y; j = blockIdx.z; }
+    else if (DIR == 1) { ix0 = blockIdx.y * LINES; k = blockIdx.z; }
+    else { ix0 = blockIdx.y * LINES; j = blockIdx.z; }
+    const int nlx = DIR == 0 ? 1 : (a.n[0] - ix0 < LINES ? a.n[0] - ix0 : LINES);   // lines present
     const long long sd = DIR == 0 ? 1LL : (DIR == 1 ? a.sy : a.sz);
-    const long long base = a.off0 + (long long)i + (long long)j * a.sy + (long long)k * a.sz;
+    const long long base0 = a.off0 + (long long)ix0 + (long long)j * a.sy + (long long)k * a.sz;
     const T* Ug = reinterpret_cast<const T*>(a.U);
     const T* Wg = reinterpret_cast<const T*>(a.W);
     const T gamma = T(a.gamma);
 
     // stage cells c0-5 .. c0+SEG+4 that exist (-3 .. nd+2)
-    for (int p = threadIdx.x; p < NC; p += NT) {
+    for (int idx = threadIdx.x; idx < LNC; idx += NT) {
+        const int p = idx / LINES, l = idx - (idx / LINES) * LINES;
         const int cell = c0 - 5 + p;
-        if (cell >= -3 && cell <= nd + 2) {
-            const long long g = base + (long long)cell * sd;
+        if (l < nlx && cell >= -3 && cell <= nd + 2) {
+            const long long g = base0 + l + (long long)cell * sd;
             T U[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) { U[v] = Ug[g + v * a.sv]; wq[v * NC + p] = Wg[g + v * a.sv]; }
+            for (int v = 0; v < NV; ++v) { U[v] = Ug[g + v * a.sv]; wq[v * LNC + idx] = Wg[g + v * a.sv]; }
             T q[NQ];
             cell_prepare<T, DIM, DIR>(U, gamma, q);
 #pragma unroll
-            for (int kk = 0; kk < NQ; ++kk) cq[kk * NC + p] = q[kk];
+            for (int kk = 0; kk < NQ; ++kk) cq[kk * LNC + idx] = q[kk];
         } else {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) wq[v * NC + p] = T(0);
+            for (int v = 0; v < NV; ++v) wq[v * LNC + idx] = T(0);
         }
     }
-    for (int idx = threadIdx.x; idx < NF * NFB; idx += NT) UF[idx] = T(0);
+    for (int idx = threadIdx.x; idx < LNF * NFB; idx += NT) UF[idx] = T(0);
     __syncthreads();
 
     // ---- per face: forward recompute and reverse -------------------------
     const T slim = T(a.slim);
     const T lam_k = T(a.c_lambda / 3600.0);
     const T eps = T(a.eps), inv_dx = T(a.inv_dx);
-    for (int f = threadIdx.x; f < NF; f += NT) {
+    for (int ff = threadIdx.x; ff < LNF; ff += NT) {
+        const int f = ff / LINES, l = ff - (ff / LINES) * LINES;
         const int face = c0 - 2 + f;            // face i' between cells i'-1 and i'
-        if (face < 0 || face > nd) continue;
-        const int p0 = f;                       // tile index of stencil cell j-2 = face-3
-        auto rec = [&](int m, int kk) -> T { return cq[kk * NC + p0 + m]; };
-        T* UFf = UF + (size_t)f * 6 * NUF;     // U and F bars of the six stencil cells
-        T* RBf = RB + (size_t)f * 2 * NRB;     // Roe-field bars of cells 2 and 3
+        if (l >= nlx || face < 0 || face > nd) continue;
+        // stencil cell j-2 = face-3 sits at position f of line l
+        auto rec = [&](int m, int kk) -> T { return cq[kk * LNC + (f + m) * LINES + l]; };
+        T* UFf = UF + (size_t)ff * 6 * NUF;    // U and F bars of the six stencil cells
+        T* RBf = RB + (size_t)ff * 2 * NRB;    // Roe-field bars of cells 2 and 3
         // cotangent of the face flux: (w_{right} - w_{left}) / dx
         T phi[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) phi[v] = (wq[v * NC + p0 + 3] - wq[v * NC + p0 + 2]) * inv_dx;
+        for (int v = 0; v < NV; ++v)
+            phi[v] = (wq[v * LNC + (f + 3) * LINES + l] - wq[v * LNC + (f + 2) * LINES + l]) * inv_dx;
 
         auto ga = [&](int kk) -> T { return rec(2, kk); };
         auto gb = [&](int kk) -> T { return rec(3, kk); };
@@ -513,10 +531,10 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
         for (int m = 0; m < 6; ++m)
 #pragma unroll
             for (int v = 0; v < NV; ++v) UFf[m * NUF + CL::U + v] += cd[m] * dUb[v];
-        SP[f * 3 + 0] += alb_m;
-        SP[f * 3 + 1] += alb_0;
-        SP[f * 3 + 2] += alb_p;
-        SL[f] = im | (i0 << 4) | (ip << 8);
+        SP[ff * 3 + 0] += alb_m;
+        SP[ff * 3 + 1] += alb_0;
+        SP[ff * 3 + 2] += alb_p;
+        SL[ff] = im | (i0 << 4) | (ip << 8);
         roe_adj<T, DIM>(ga, gb, gamma, r, rb, RBf, RBf + NRB);
     }
     __syncthreads();
@@ -525,12 +543,13 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
     T* Gg = reinterpret_cast<T*>(a.G);
     T* ghost = reinterpret_cast<T*>(a.ghost);
     const bool first = c0 == 0, last = c0 + SEG >= nd;
-    for (int p = threadIdx.x; p < SEG + 6; p += NT) {
+    for (int idx = threadIdx.x; idx < LINES * (SEG + 6); idx += NT) {
+        const int p = idx / LINES, l = idx - (idx / LINES) * LINES;
         const int cell = c0 - 3 + p;   // owned cells c0..c0+SEG-1 and boundary ghosts
         const bool owned = cell >= c0 && cell < c0 + SEG && cell < nd;
         const bool gl = first && cell < 0 && cell >= -3;
         const bool gr = last && cell >= nd && cell <= nd + 2;
-        if (!owned && !gl && !gr) continue;
+        if (l >= nlx || (!owned && !gl && !gr)) continue;
         T qb[NQ];
 #pragma unroll
         for (int kk = 0; kk < NQ; ++kk) qb[kk] = T(0);
@@ -538,35 +557,37 @@ __global__ void __launch_bounds__(VjpTile<DIM>::NT) k_vjp(VjpArgs a)
             if (fi < 0 || fi > nd) continue;
             const int f = fi - (c0 - 2);
             if (f < 0 || f >= NF) continue;
+            const int ff = f * LINES + l;
             const int m = cell - fi + 3;
             // the entries this cell receives from face fi, in the record
             // layout; the others are zero for it
-            const T* uf = UF + ((size_t)f * 6 + m) * NUF;
+            const T* uf = UF + ((size_t)ff * 6 + m) * NUF;
 #pragma unroll
             for (int kk = 0; kk < NUF; ++kk) qb[kk] += uf[kk];
             if (m == 2 || m == 3) {
-                const T* rbp = RB + ((size_t)f * 2 + (m - 2)) * NRB;
+                const T* rbp = RB + ((size_t)ff * 2 + (m - 2)) * NRB;
 #pragma unroll
                 for (int kk = 0; kk < NRB; ++kk) qb[CL::SU + kk] += rbp[kk];
             }
-            const int sl = SL[f];
-            if ((sl & 15) == m) qb[CL::LM] += SP[f * 3 + 0];
-            if (((sl >> 4) & 15) == m) qb[CL::L0] += SP[f * 3 + 1];
-            if (((sl >> 8) & 15) == m) qb[CL::LP] += SP[f * 3 + 2];
+            const int sl = SL[ff];
+            if ((sl & 15) == m) qb[CL::LM] += SP[ff * 3 + 0];
+            if (((sl >> 4) & 15) == m) qb[CL::L0] += SP[ff * 3 + 1];
+            if (((sl >> 8) & 15) == m) qb[CL::LP] += SP[ff * 3 + 2];
         }
         const int pc = cell - (c0 - 5);
         T U[NV], Ub[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) U[v] = cq[(CL::U + v) * NC + pc];
+        for (int v = 0; v < NV; ++v) U[v] = cq[(CL::U + v) * LNC + pc * LINES + l];
         cell_adj<T, DIM, DIR>(U, gamma, qb, Ub);
         if (owned) {
-            const long long g = base + (long long)cell * sd;
+            const long long g = base0 + l + (long long)cell * sd;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 if (a.accumulate) Gg[g + v * a.sv] += Ub[v];
                 else Gg[g + v * a.sv] = Ub[v];
             }
         } else {
+            const long long i = ix0 + l;
             const long long line = DIR == 0 ? ((long long)k * a.n[1] + j)
                                             : (DIR == 1 ? ((long long)k * a.n[0] + i) : ((long long)j * a.n[0] + i));
             const int slot = gl ? (-cell - 1) : (3 + cell - nd);   // 0..2 left (-1,-2,-3), 3..5 right

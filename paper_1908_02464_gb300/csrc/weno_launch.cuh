@@ -166,7 +166,7 @@ cudaError_t launch_pack_t(const void* src, void* dst, int nv, const int* n, long
 template <typename T, int DIM, int DIR>
 cudaError_t launch_vjp_one(const VjpArgs& a, cudaStream_t s)
 {
-    using SM = VjpSmem<T, DIM>;
+    using SM = VjpSmem<T, DIM, DIR>;
     auto kern = k_vjp<T, DIM, DIR>;
     static bool configured = false;
     if (!configured) {
@@ -175,11 +175,12 @@ cudaError_t launch_vjp_one(const VjpArgs& a, cudaStream_t s)
         configured = true;
     }
     int e0, e1;
+    // y and z tiles hold SM::LINES lines consecutive in x
     if (DIR == 0) { e0 = a.n[1]; e1 = a.n[2]; }
-    else if (DIR == 1) { e0 = a.n[0]; e1 = a.n[2]; }
-    else { e0 = a.n[0]; e1 = a.n[1]; }
+    else if (DIR == 1) { e0 = (a.n[0] + SM::LINES - 1) / SM::LINES; e1 = a.n[2]; }
+    else { e0 = (a.n[0] + SM::LINES - 1) / SM::LINES; e1 = a.n[1]; }
     dim3 grid((a.n[DIR] + SM::SEG - 1) / SM::SEG, e0, e1);
-    kern<<<grid, VjpTile<DIM>::NT, SM::bytes, s>>>(a);
+    kern<<<grid, VjpTile<T, DIM, DIR>::NT, SM::bytes, s>>>(a);
     return cudaGetLastError();
 }
 
