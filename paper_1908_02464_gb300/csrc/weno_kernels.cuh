@@ -991,19 +991,27 @@ static __global__ void k_totals_final(const double* partial, int nblk, int nv, d
 }
 
 // --------------------------------------- interior <-> ghosted layout copies
+// One work unit is up to blockDim.x consecutive cells of one row (variable
+// v, rows j, k) of the interior-only array, whose index is row * nx + i with
+// row = (v nz + k) ny + j.  The index arithmetic is done once per unit; the
+// threads of a block copy consecutive cells, coalesced on both sides.
 template <typename T>
 __global__ void k_pack(const T* src, T* dst, int nv, int nx, int ny, int nz, long long sy, long long sz,
                        long long sv, long long off0, int to_ghosted)
 {
-    const long long cells = (long long)nx * ny * nz;
-    const long long total = cells * nv;
-    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-         id += (long long)gridDim.x * blockDim.x) {
-        const long long v = id / cells, c = id % cells;
-        const long long i = c % nx, j = (c / nx) % ny, k = c / ((long long)nx * ny);
+    const int chunks = (nx + blockDim.x - 1) / blockDim.x;
+    const long long plane = (long long)ny * nz;
+    const long long units = (long long)nv * plane * chunks;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const long long row = u / chunks;
+        const int i = (int)(u - row * chunks) * blockDim.x + threadIdx.x;
+        if (i >= nx) continue;
+        const long long v = row / plane, jk = row - v * plane;
+        const long long k = jk / ny, j = jk - k * ny;
+        const long long lin = row * nx + i;
         const long long g = off0 + i + j * sy + k * sz + v * sv;
-        if (to_ghosted) dst[g] = src[id];
-        else dst[id] = src[g];
+        if (to_ghosted) dst[g] = src[lin];
+        else dst[lin] = src[g];
     }
 }
 

@@ -156,8 +156,9 @@ template <typename T>
 cudaError_t launch_pack_t(const void* src, void* dst, int nv, const int* n, long long sy, long long sz,
                           long long sv, long long off0, int to_ghosted, int nsm, cudaStream_t s)
 {
-    const long long total = (long long)nv * n[0] * n[1] * n[2];
-    const int blocks = grid_for(total, 256, nsm * 16);
+    // units of 256 consecutive cells of one row (see k_pack)
+    const long long units = (long long)nv * n[1] * n[2] * ((n[0] + 255) / 256);
+    const int blocks = (int)(units < (long long)nsm * 16 ? units : (long long)nsm * 16);
     k_pack<T><<<blocks, 256, 0, s>>>(reinterpret_cast<const T*>(src), reinterpret_cast<T*>(dst), nv, n[0],
                                       n[1], n[2], sy, sz, sv, off0, to_ghosted);
     return cudaGetLastError();
