@@ -589,3 +589,32 @@ def test_mach2000_jet_runs_to_the_end_under_the_lambda_reading():
     U = np.ascontiguousarray(U)
     st, t, k = orc.advance(prob, U, 0.0, prob["t_end"])
     assert st == 3 and k < 100   # non-physical state
+
+
+def test_switch_threshold_is_monotone_in_the_characteristic_length():
+    """eps_h = C (dx / L)^alpha (Sec. 3) falls as L grows: on fixed data the
+    faces taking the WENO flux at L are a subset of those at 2 L, all faces
+    are smooth for L small enough and none for L large enough (on data
+    whose detector values are nonzero).  A wrong power, a dx L product or an
+    inverted comparison breaks one of these."""
+    prob, U = P.random_state(1, [300], seed=21, kind="mixed")
+    prev = None
+    counts = []
+    for L in (1e-4, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0, 1e6):
+        pr = dict(prob)
+        pr["L_char"] = L
+        _, flags, _ = orc.rhs(pr, U, 0.0, want_flags=True)
+        weno = flags == 0
+        if prev is not None:
+            assert np.all(weno[prev]), L
+        prev = weno
+        counts.append(int(weno.sum()))
+    assert counts[0] == 0
+    assert counts[-1] == len(prev)
+    assert counts[1] < counts[-2]
+    # C scales the threshold like L^-alpha: C = 2^3 at L = 2 gives the flags of L = 1
+    pr1 = dict(prob); pr1["L_char"] = 1.0
+    pr2 = dict(prob); pr2["L_char"] = 2.0; pr2["C_thr"] = 8.0
+    _, f1, _ = orc.rhs(pr1, U, 0.0, want_flags=True)
+    _, f2, _ = orc.rhs(pr2, U, 0.0, want_flags=True)
+    assert np.array_equal(f1, f2)
