@@ -11,7 +11,7 @@ with the RK combination fused); one step is 3 cell-updates per cell.
 state and reported with their L1/Linf density error against the FP64 path
 after the same number of steps.  L2 is flushed (256 MiB write) between timed
 steps.  `--impl reference` times the FP64 CPU oracle (the reference arm of
-this project) on the same grid from the initial condition.
+this project) on the same developed state.
 """
 from __future__ import annotations
 
@@ -41,6 +41,10 @@ T_DEVELOP = 0.05
 # linear-upwind face and per WENO face, by dimension.  The flux divergence
 # adds 2 flops per variable per cell.
 ALG_FLOPS = {1: (18, 158, 1139), 2: (22, 221, 1625), 3: (26, 292, 2167)}
+# The same counts without the operations the oracle folds between known
+# constants (e.g. 13/12) and without products, sums and quotients with
+# structural 0 or +-1 entries (of the eigenvector matrices, E_2 = E_3 = 0).
+ALG_FLOPS_ESSENTIAL = {1: (17, 151, 1060), 2: (21, 203, 1451), 3: (25, 255, 1842)}
 FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA lanes per SM per clock on GB300
 FP32_FLOP_PER_CLK_SM = 256    # 128 FFMA lanes per SM per clock
 
@@ -150,11 +154,33 @@ def shard(count: int, rank: int, world: int):
     return list(range(rank, count, world))
 
 
-def sweep_flops(dim: int, n, weno_faces: int, d: int) -> float:
-    fc, fu, fw = ALG_FLOPS[dim]
+def sweep_flops(dim: int, n, weno_faces: int, d: int, table=None) -> float:
+    fc, fu, fw = (table or ALG_FLOPS)[dim]
     cells = float(np.prod(n))
     faces = cells / n[d] * (n[d] + 1)
     return cells * (fc + 2 * (dim + 2)) + faces * fu + weno_faces * (fw - fu)
+
+
+def workload_config(ws: int) -> dict:
+    """The timed workload, identical for both arms (no measured values)."""
+    return {"workload": f"double Mach reflection {NX}x{NY} (Sec. 4.5), FP64, state developed from t=0 to "
+                        f"t={T_DEVELOP} (untimed), LLF splitting, hybrid on, TVD RK3 CFL 0.5",
+            "grid": [NX, NY], "cells": NX * NY, "precision": "fp64", "t_start": T_DEVELOP,
+            "parallelism": f"replicas x{ws}", "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def developed_state(stream=None):
+    """The benchmark's input: the double Mach reflection advanced from its
+    initial condition to t = T_DEVELOP by the library (FP64, untimed).
+    Returns the solver holding it and the state as a device tensor."""
+    from paper_1908_02464_gb300 import problems as P
+    from paper_1908_02464_gb300 import weno
+    prob, U0 = P.double_mach(NX, NY)
+    s = weno.Solver(prob, "fp64", stream=stream)
+    s.set_state(U0)
+    s.advance(T_DEVELOP)
+    Udev, t_dev = s.get_state(device=True)
+    return s, Udev, t_dev
 
 
 # ---------------------------------------------------------------- our arm
@@ -179,10 +205,8 @@ def run_ours(args) -> dict:
     clocks = ClockSampler(dev)
     clocks.start()
     # developed state (untimed)
-    s64 = weno.Solver(prob, "fp64", stream=stream)
-    s64.set_state(U0)
-    s64.advance(T_DEVELOP)
-    Udev, t_dev = s64.get_state(device=True)
+    s64, Udev, t_dev = developed_state(stream)
+    Udev_host = np.ascontiguousarray(Udev.cpu().numpy())
     flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device="cuda")   # 256 MiB
 
     tiles = {}
@@ -222,11 +246,13 @@ def run_ours(args) -> dict:
     torch.cuda.nvtx.range_pop()
     dom = int(np.argmax(ms_dir))
     fl = sweep_flops(2, [NX, NY], wf_dir[dom], dom)
+    fl_ess = sweep_flops(2, [NX, NY], wf_dir[dom], dom, ALG_FLOPS_ESSENTIAL)
     achieved = fl / (ms_dir[dom] * 1e-3)
     peak64 = nsm * FP64_FLOP_PER_CLK_SM * sm_max * 1e6
     micro64, _ = weno.weno_measure_fma_peak(0)
     traffic = None
     pipe_ncu = None
+    executed = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         with open(tp) as f:
@@ -234,6 +260,13 @@ def run_ours(args) -> dict:
         if tj.get("csrc_digest") == csrc_digest():
             traffic = tj.get("fp64", {}).get(f"sweep_dir{dom}")
             pipe_ncu = tj.get("fp64", {}).get("pipe_fp64_pct_active", {}).get(f"sweep_dir{dom}")
+            mix = tj.get("fp64", {}).get("thread_inst", {}).get(f"sweep_dir{dom}")
+            if mix:
+                # executed FP64 flops of the captured launch (DFMA = 2) over the event time
+                ex = mix["dadd"] + mix["dmul"] + 2.0 * mix["dfma"]
+                executed = {"flops_per_launch": ex, "achieved": ex / (ms_dir[dom] * 1e-3) / 1e12,
+                            "frac": ex / (ms_dir[dom] * 1e-3) / peak64,
+                            "source": "ncu thread-instruction counts (DADD + DMUL + 2 DFMA), profiles/traffic.json"}
     hbm_peak = None
     mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(mp):
@@ -241,6 +274,9 @@ def run_ours(args) -> dict:
             hbm_peak = json.load(f).get("hbm_gbs")
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak64, "traffic": traffic,
+                "achieved_essential": fl_ess / (ms_dir[dom] * 1e-3) / 1e12,
+                "frac_essential": fl_ess / (ms_dir[dom] * 1e-3) / peak64,
+                "alg_flops_essential_per_launch": fl_ess, "executed": executed,
                 "kernel": f"k_sweep<double,2,{dom}> ({'x' if dom == 0 else 'y'}-sweep)",
                 "kernel_ms": ms_dir[dom], "alg_flops_per_launch": fl, "weno_faces_per_launch": int(wf_dir[dom]),
                 "peak_source": f"derived: {nsm} SMs x {FP64_FLOP_PER_CLK_SM} FP64 flop/clk x {sm_max:.0f} MHz",
@@ -316,12 +352,9 @@ def run_ours(args) -> dict:
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"double Mach reflection {NX}x{NY} (Sec. 4.5), FP64, state developed on the GPU "
-                                  f"from t=0 to t={T_DEVELOP}, LLF splitting, hybrid on, TVD RK3 CFL 0.5",
-                      "grid": [NX, NY], "cells": cells, "precision": "fp64", "parallelism": f"replicas x{ws}",
-                      "l2": "flushed between timed steps (256 MiB write)",
-                      "weno_face_fraction": weno_frac, "t_start": t_dev, "t_after": t64,
-                      "tiles_autotuned": tiles},
+           "config": workload_config(ws),
+           "workload_stats": {"weno_face_fraction": weno_frac, "t_start": t_dev, "t_after": t64,
+                              "tiles_autotuned": tiles},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
            "clocks": clk, "ms_per_step_all": ms64}
     res.update(extra)
@@ -336,7 +369,7 @@ def run_ours(args) -> dict:
     if thr is not None:
         res["threshold_study_shu_osher_400"] = thr
     if rank == 0 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(args)
+        res["cpu_baseline"] = cpu_baseline(args, Udev_host, t_dev)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return res if rank == 0 else None
@@ -566,15 +599,25 @@ def vortex3d_rhs_vjp(args) -> dict:
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_steps(nsteps: int, U=None, t=0.0):
+def oracle_steps(nsteps: int, U, t: float):
+    """Time `nsteps` oracle RK3 steps of the benchmark grid from (U, t), in
+    place.  Returns (seconds, U, t)."""
     from oracle import oracle as orc
     from paper_1908_02464_gb300 import problems as P
-    prob, U0 = P.double_mach(NX, NY)
-    U = U0 if U is None else U
+    prob, _ = P.double_mach(NX, NY)
     t0 = time.perf_counter()
     for _ in range(nsteps):
         st, t, dt = orc.step(prob, U, t, 1.0)
     return time.perf_counter() - t0, U, t
+
+
+def oracle_weno_fraction(U, t: float) -> float:
+    """Fraction of faces on which the oracle takes the WENO flux at (U, t)."""
+    from oracle import oracle as orc
+    from paper_1908_02464_gb300 import problems as P
+    prob, _ = P.double_mach(NX, NY)
+    _, flags, _ = orc.rhs(prob, U, t, want_flags=True)
+    return float(1.0 - np.mean(flags))
 
 
 def host_info() -> dict:
@@ -593,72 +636,91 @@ def host_info() -> dict:
     return {"host_cores": os.cpu_count(), "cpu_model": model or platform.machine()}
 
 
-def oracle_worker(steps: int) -> None:
-    """One single-threaded oracle process of the all-core baseline: prints
-    the wall-clock start and end of its timed steps as one JSON line."""
-    from oracle import oracle as orc
-    from paper_1908_02464_gb300 import problems as P
-    prob, U = P.double_mach(NX, NY)
+def oracle_worker(steps: int, state_path: str, t: float) -> None:
+    """One single-threaded oracle process of the all-core baseline: loads the
+    developed state, times its steps and prints the wall-clock start and end
+    as one JSON line."""
+    U = np.ascontiguousarray(np.load(state_path))
     t0 = time.time()
-    t = 0.0
-    for _ in range(steps):
-        st, t, dt = orc.step(prob, U, t, 1.0)
+    oracle_steps(steps, U, t)
     print(json.dumps({"start": t0, "end": time.time()}), flush=True)
 
 
-def cpu_all_cores(steps: int) -> dict:
+def cpu_all_cores(steps: int, U, t: float) -> dict:
     """The unmodified single-threaded oracle run as one process per host
-    core, all at once, each on its own copy of the workload; throughput =
-    all processes' cell-updates / (last end - first start)."""
+    core, all at once, each on its own copy of the developed state;
+    throughput = all processes' cell-updates / (last end - first start)."""
     n = os.cpu_count() or 1
-    cmd = [sys.executable, "-c", f"import bench; bench.oracle_worker({int(steps)})"]
-    procs = [subprocess.Popen(cmd, cwd=ROOT, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-             for _ in range(n)]
-    spans = []
-    for p in procs:
-        out, _ = p.communicate()
-        if p.returncode == 0 and out.strip():
-            spans.append(json.loads(out.strip().splitlines()[-1]))
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    np.save(path, U)
+    try:
+        cmd = [sys.executable, "-c", f"import bench; bench.oracle_worker({int(steps)}, {path!r}, {float(t)!r})"]
+        procs = [subprocess.Popen(cmd, cwd=ROOT, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 for _ in range(n)]
+        spans = []
+        for p in procs:
+            out, _ = p.communicate()
+            if p.returncode == 0 and out.strip():
+                spans.append(json.loads(out.strip().splitlines()[-1]))
+    finally:
+        os.unlink(path)
     if len(spans) != n:
         return {"unavailable": f"{n - len(spans)} of {n} oracle processes failed"}
     wall = max(x["end"] for x in spans) - min(x["start"] for x in spans)
     return {"value": 3.0 * NX * NY * steps * n / wall, "unit": UNIT, "cores": n, "kind": "oracle",
             "sample": f"{n} concurrent single-threaded oracle processes, each {steps} FP64 RK3 steps of the "
-                      f"{NX}x{NY} double Mach reflection from its initial condition ({wall:.1f} s wall)"}
+                      f"{NX}x{NY} double Mach reflection from the developed state t = {t:.4f} ({wall:.1f} s wall)"}
 
 
-def cpu_baseline(args) -> dict:
+def cpu_baseline(args, U, t: float) -> dict:
+    """The oracle as it stands on one host core, timed on the developed state
+    the GPU arm times (a bounded sample: `--cpu-steps` RK3 steps)."""
     steps = args.cpu_steps
-    el, _, _ = oracle_steps(steps)
+    wf = oracle_weno_fraction(U, t)
+    el, _, _ = oracle_steps(steps, U.copy(), t)
     out = {"value": 3.0 * NX * NY * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{steps} FP64 RK3 steps of the {NX}x{NY} double Mach reflection from its initial "
-                     f"condition, single-threaded C++ oracle ({el:.1f} s)", **host_info()}
-    out["all_cores"] = cpu_all_cores(max(1, steps // 4))
+           "sample": f"{steps} FP64 RK3 steps of the {NX}x{NY} double Mach reflection from the developed state "
+                     f"t = {t:.4f} (the GPU arm's), single-threaded C++ oracle ({el:.1f} s)",
+           "weno_face_fraction_at_start": wf, **host_info()}
+    out["all_cores"] = cpu_all_cores(max(1, steps // 4), U, t)
     return out
 
 
 def run_reference(args) -> dict | None:
+    """The reference arm: the FP64 oracle timed on the same workload as the
+    GPU arm.  Its input, the state developed to t = T_DEVELOP, is prepared
+    by the library on the GPU, untimed: the oracle would need about 1000 steps
+    of the full grid (about 12 minutes of one core) to reach it.  Without a
+    GPU the arm reports itself unavailable."""
     ws, rank, local = dist_env()
     if rank != 0:
         return None
+    import torch
+    if not torch.cuda.is_available():
+        return {"impl": "reference", "unavailable": "the timed state is prepared on the GPU and none is visible"}
     from oracle import oracle as orc
     orc.build()
-    from paper_1908_02464_gb300 import problems as P
-    prob, U = P.double_mach(NX, NY)
-    t = 0.0
-    for _ in range(args.warmup):
-        st, t, dt = orc.step(prob, U, t, 1.0)
+    from paper_1908_02464_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(local)
+    s, Udev, t_dev = developed_state()
+    U = np.ascontiguousarray(Udev.cpu().numpy())
+    s.close()
+    del Udev
+    wf = oracle_weno_fraction(U, t_dev)
+    _, U, t = oracle_steps(args.warmup, U, t_dev)
     el, U, t = oracle_steps(args.steps, U, t)
     v = 3.0 * NX * NY * args.steps / el
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"double Mach reflection {NX}x{NY} (Sec. 4.5), FP64, from the initial "
-                                   "condition, LLF splitting, hybrid on, TVD RK3 CFL 0.5",
-                       "grid": [NX, NY], "cells": NX * NY, "precision": "fp64"},
+            "config": workload_config(ws),
+            "workload_stats": {"weno_face_fraction_at_start": wf, "t_start": t_dev, "t_after": t,
+                               "input": "developed state prepared by the library on the GPU, untimed"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.warmup}+{args.steps} RK3 steps of the full grid from t=0",
-                             **host_info()},
+                             "sample": f"{args.warmup}+{args.steps} RK3 steps of the full grid from the developed "
+                                       f"state t = {t_dev:.4f}", **host_info()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

@@ -299,10 +299,11 @@ weno_status weno_batch_solve(const weno_batch_desc* desc, const weno_params* par
 
 /* Allocation-free conserved totals (the paper has no counterpart; this is a
  * service for callers that cannot allocate device memory where they need
- * the totals: code running while a stream is being captured into a CUDA
- * graph, applications whose device memory belongs to their own pool, loops
- * with a fixed memory budget).  Same sums as weno_conserved_totals, for a
- * state the caller owns and without a context; nothing is allocated.
+ * the totals: applications whose device memory belongs to their own pool or
+ * allocator, and time-stepping loops with a fixed memory budget that must
+ * neither allocate nor take the device-wide synchronization cudaMalloc can
+ * imply).  Same sums as weno_conserved_totals, for a state the caller owns
+ * and without a context; nothing is allocated.
  *   dim, n[dim], dx[dim]: grid (cells per direction, spacing); the result is
  *       sum_cells U dV with dV = prod dx.
  *   precision: element type of U_dev (double for WENO_FP64, float else).
@@ -315,7 +316,9 @@ weno_status weno_batch_solve(const weno_batch_desc* desc, const weno_params* par
  * cells are rejected with WENO_ERR_INVALID_ARG, as are a bad dim, n < 1, an
  * unknown precision or a NULL pointer.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Each call
+ * current, and so does every later call made outside stream capture (the
+ * address changes if the device is reset); make the first call before any
+ * stream capture.  Each call
  * overwrites the partial sums it uses before reading them, but all calls on a
  * device share the one array: calls that overlap on the GPU (different
  * streams without ordering) race.  Asynchronous; WENO_ERR_CUDA if the

@@ -281,20 +281,26 @@ def totals(problem: dict, U: np.ndarray) -> np.ndarray:
     return out
 
 
-def count_cell(problem: dict, d: int, U) -> np.ndarray:
+def count_cell(problem: dict, d: int, U, essential: bool = False) -> np.ndarray:
+    """(add/sub, mul, div, sqrt) of one cell's quantities as written, or with
+    essential=True without operations folded between known constants and
+    without products / sums / quotients with structural 0 or +-1."""
     c = make_cfg(problem)
     U = np.ascontiguousarray(U, dtype=np.float64)
-    out = (ctypes.c_longlong * 4)()
+    out = (ctypes.c_longlong * 8)()
     lib().or_count_cell(ctypes.byref(c), d, _dp(U), out)
-    return np.array(list(out))
+    out = np.array(list(out))
+    return out[4:] if essential else out[:4]
 
 
-def count_face(problem: dict, d: int, U6, eps_h: float):
+def count_face(problem: dict, d: int, U6, eps_h: float, essential: bool = False):
+    """Operation counts of one face (see count_cell) and its smooth flag."""
     c = make_cfg(problem)
     U6 = np.ascontiguousarray(U6, dtype=np.float64)
-    out = (ctypes.c_longlong * 4)()
+    out = (ctypes.c_longlong * 8)()
     smooth = lib().or_count_face(ctypes.byref(c), d, eps_h, _dp(U6), out)
-    return np.array(list(out)), bool(smooth)
+    out = np.array(list(out))
+    return (out[4:] if essential else out[:4]), bool(smooth)
 
 
 def riemann_star(gamma: float, WL, WR):

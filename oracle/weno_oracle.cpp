@@ -90,25 +90,58 @@ static const int NG = 3;  /* ghost layers */
 /* ------------------------------------------------------------------ */
 /* operation-counting real type (for the algorithmic flop counts)      */
 /* ------------------------------------------------------------------ */
+/* Two tallies per operation kind:
+ * - all operations as written (the algorithmic count);
+ * - the essential ones: an operation whose operands are both known
+ *   constants (built from literals or configuration values) is folded, a
+ *   product with a known 0 or +-1, a sum with a known 0 and a quotient by a
+ *   known +-1 are structural; neither is counted.  A product with a known 0
+ *   is itself a known 0. */
 struct OpCount { long long add, mul, div, sqrt_; };
-static OpCount g_ops;
+static OpCount g_ops, g_ess;
 
 struct Cnt {
     double v;
-    Cnt() : v(0) {}
-    Cnt(double x) : v(x) {}
+    bool k;     /* known constant */
+    Cnt() : v(0), k(true) {}
+    Cnt(double x) : v(x), k(true) {}
 };
-static inline Cnt operator+(Cnt a, Cnt b) { g_ops.add++; return Cnt(a.v + b.v); }
-static inline Cnt operator-(Cnt a, Cnt b) { g_ops.add++; return Cnt(a.v - b.v); }
-static inline Cnt operator*(Cnt a, Cnt b) { g_ops.mul++; return Cnt(a.v * b.v); }
-static inline Cnt operator/(Cnt a, Cnt b) { g_ops.div++; return Cnt(a.v / b.v); }
-static inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+static inline Cnt cnt_data(double x) { Cnt c(x); c.k = false; return c; }
+static inline bool known(Cnt a, double x) { return a.k && a.v == x; }
+static inline Cnt cnt_res(double v, bool k) { Cnt c(v); c.k = k; return c; }
+static inline Cnt cnt_add(Cnt a, Cnt b, double r)
+{
+    g_ops.add++;
+    if (!(a.k && b.k) && !known(a, 0.0) && !known(b, 0.0)) g_ess.add++;
+    return cnt_res(r, a.k && b.k);
+}
+static inline Cnt operator+(Cnt a, Cnt b) { return cnt_add(a, b, a.v + b.v); }
+static inline Cnt operator-(Cnt a, Cnt b) { return cnt_add(a, b, a.v - b.v); }
+static inline Cnt operator*(Cnt a, Cnt b)
+{
+    g_ops.mul++;
+    if (known(a, 0.0) || known(b, 0.0)) return Cnt(0.0);
+    if (!(a.k && b.k) && !known(a, 1.0) && !known(a, -1.0) && !known(b, 1.0) && !known(b, -1.0)) g_ess.mul++;
+    return cnt_res(a.v * b.v, a.k && b.k);
+}
+static inline Cnt operator/(Cnt a, Cnt b)
+{
+    g_ops.div++;
+    if (!(a.k && b.k) && !known(b, 1.0) && !known(b, -1.0)) g_ess.div++;
+    return cnt_res(a.v / b.v, a.k && b.k);
+}
+static inline Cnt operator-(Cnt a) { return cnt_res(-a.v, a.k); }
 static inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
 static inline bool operator<(Cnt a, Cnt b) { return a.v < b.v; }
 static inline bool operator>(Cnt a, Cnt b) { return a.v > b.v; }
 static inline bool operator<=(Cnt a, Cnt b) { return a.v <= b.v; }
-static inline Cnt sqrt_r(Cnt a) { g_ops.sqrt_++; return Cnt(std::sqrt(a.v)); }
-static inline Cnt abs_r(Cnt a) { return Cnt(std::fabs(a.v)); }
+static inline Cnt sqrt_r(Cnt a)
+{
+    g_ops.sqrt_++;
+    if (!a.k) g_ess.sqrt_++;
+    return cnt_res(std::sqrt(a.v), a.k);
+}
+static inline Cnt abs_r(Cnt a) { return cnt_res(std::fabs(a.v), a.k); }
 static inline double val(Cnt a) { return a.v; }
 
 /* forward-mode dual number (value, derivative) for Jacobian-vector products;
@@ -1050,19 +1083,27 @@ void or_totals(const or_cfg* c, const double* U, double* tot)
     }
 }
 
-/* algorithmic operation counts: out[0..3] = add/sub, mul, div, sqrt.
+/* algorithmic operation counts: out[0..3] = add/sub, mul, div, sqrt as
+ * written; out[4..7] = the essential ones (see Cnt).
  * or_count_cell: per-cell quantities of one cell;
  * or_count_face: one face from six states (cell work excluded); returns the
  * smooth flag so the caller can classify the count (linear or WENO face). */
+static void put_counts(long long* out)
+{
+    out[0] = g_ops.add; out[1] = g_ops.mul; out[2] = g_ops.div; out[3] = g_ops.sqrt_;
+    out[4] = g_ess.add; out[5] = g_ess.mul; out[6] = g_ess.div; out[7] = g_ess.sqrt_;
+}
+
 void or_count_cell(const or_cfg* c, int d, const double* U, long long* out)
 {
     int nv = nvar_of(*c);
     Cnt Uc[5];
-    for (int v = 0; v < nv; ++v) Uc[v] = Cnt(U[v]);
+    for (int v = 0; v < nv; ++v) Uc[v] = cnt_data(U[v]);
     g_ops = OpCount{0, 0, 0, 0};
+    g_ess = OpCount{0, 0, 0, 0};
     CellQ<Cnt> q;
     cell_quantities(*c, d, Uc, q);
-    out[0] = g_ops.add; out[1] = g_ops.mul; out[2] = g_ops.div; out[3] = g_ops.sqrt_;
+    put_counts(out);
 }
 
 int or_count_face(const or_cfg* c, int d, double eps_h, const double* U6, long long* out)
@@ -1071,15 +1112,16 @@ int or_count_face(const or_cfg* c, int d, double eps_h, const double* U6, long l
     CellQ<Cnt> S[6];
     for (int m = 0; m < 6; ++m) {
         Cnt Uc[5];
-        for (int v = 0; v < nv; ++v) Uc[v] = Cnt(U6[m * nv + v]);
+        for (int v = 0; v < nv; ++v) Uc[v] = cnt_data(U6[m * nv + v]);
         cell_quantities(*c, d, Uc, S[m]);
     }
     double zeros[5] = {0, 0, 0, 0, 0};
     Cnt Fh[5];
     FaceInfo info;
     g_ops = OpCount{0, 0, 0, 0};
+    g_ess = OpCount{0, 0, 0, 0};
     face_flux(*c, d, eps_h, S, zeros, Fh, &info);
-    out[0] = g_ops.add; out[1] = g_ops.mul; out[2] = g_ops.div; out[3] = g_ops.sqrt_;
+    put_counts(out);
     return info.smooth;
 }
 

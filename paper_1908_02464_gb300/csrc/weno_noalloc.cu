@@ -7,11 +7,11 @@
 // holds until the process exits.
 //
 // Who needs it: callers that cannot call cudaMalloc at the point where they
-// want the totals -- code running while a stream is being captured into a
-// CUDA graph (allocation is not allowed there), applications whose device
-// memory belongs to their own pool or allocator, and loops with a fixed
-// memory budget that must not allocate.  Such a caller passes the state and
-// a device buffer for the result; nothing else is needed.
+// want the totals -- applications whose device memory belongs to their own
+// pool or allocator, and time-stepping loops with a fixed memory budget that
+// must not allocate (cudaMalloc can also synchronize the device, which such
+// a loop cannot afford mid-step).  Such a caller passes the state and a
+// device buffer for the result; nothing else is needed.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -85,20 +85,28 @@ cudaError_t launch_totals(const void* U, long long cells, int nblk, double dV, d
     return cudaGetLastError();
 }
 
-// Device address of the scratch array for the current device, looked up once
-// per device with that device current.
-cudaError_t scratch_for_current_device(double** out)
+// Device address of the scratch array for the current device.  The address
+// is looked up (cudaGetSymbolAddress, with the device current) on every call
+// made while `s` is not being captured, so a module reloaded after a device
+// reset is found again; while `s` is being captured the address cached by
+// the last lookup on this device is used, and without one the call fails.
+cudaError_t scratch_for_current_device(cudaStream_t s, double** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_partial_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[dev] = static_cast<double*>(p);
+    } else if (g_scratch_addr[dev] == nullptr) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_scratch_addr[dev];
     return cudaSuccess;
@@ -114,15 +122,15 @@ extern "C" weno_status weno_conserved_totals_noalloc(int dim, const int* n, cons
     long long cells = 1;
     double dV = 1.0;
     for (int d = 0; d < dim; ++d) {
-        if (n[d] < 1) return WENO_ERR_INVALID_ARG;
+        // cells stays <= kMaxCells, so the product cannot overflow
+        if (n[d] < 1 || n[d] > kMaxCells / cells) return WENO_ERR_INVALID_ARG;
         cells *= n[d];
         dV *= dx[d];
     }
-    if (cells > kMaxCells) return WENO_ERR_INVALID_ARG;
-    double* scratch = nullptr;
-    if (scratch_for_current_device(&scratch) != cudaSuccess) return WENO_ERR_CUDA;
-    const int nblk = (int)((cells + kChunk - 1) / kChunk);
     cudaStream_t s = (cudaStream_t)stream;
+    double* scratch = nullptr;
+    if (scratch_for_current_device(s, &scratch) != cudaSuccess) return WENO_ERR_CUDA;
+    const int nblk = (int)((cells + kChunk - 1) / kChunk);
     cudaError_t e;
     const bool f64 = precision == WENO_FP64;
     if (dim == 1) e = f64 ? launch_totals<double, 3>(U_dev, cells, nblk, dV, scratch, totals_dev, s)

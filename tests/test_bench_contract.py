@@ -15,6 +15,23 @@ def test_algorithmic_flop_table_matches_oracle_counts():
         fw, s2 = orc.count_face(prob, 0, U6, -1.0)
         assert s1 and not s2
         assert bench.ALG_FLOPS[dim] == (c, fu.sum(), fw.sum())
+        ce = orc.count_cell(prob, 0, U, essential=True).sum()
+        fue, _ = orc.count_face(prob, 0, U6, 1e300, essential=True)
+        fwe, _ = orc.count_face(prob, 0, U6, -1.0, essential=True)
+        assert bench.ALG_FLOPS_ESSENTIAL[dim] == (ce, fue.sum(), fwe.sum())
+
+
+def test_essential_counts_leave_out_only_folded_and_structural_operations():
+    """One Euler cell: the essential count drops only the first sum of
+    |u|^2 = 0 + u u, which starts from a known zero."""
+    prob = dict(dim=1, n=[8], lo=[0], hi=[1], bc_lo=[0], bc_hi=[0])
+    U = np.array([1.0, 0.3, 3.0])
+    for essential in (False, True):
+        c = orc.count_cell(prob, 0, U, essential=essential)
+        assert c[3] == 1                      # one square root (sound speed) either way
+    w = orc.count_cell(prob, 0, U)
+    e = orc.count_cell(prob, 0, U, essential=True)
+    assert np.all(e <= w) and e.sum() == w.sum() - 1 and e[0] == w[0] - 1
 
 
 def test_sweep_flops_formula():

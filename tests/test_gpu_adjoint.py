@@ -7,6 +7,7 @@ import pytest
 
 from oracle import oracle as orc
 from paper_1908_02464_gb300 import problems as P
+from tests import parity_log
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -41,7 +42,10 @@ def test_vjp_dot_product_identity_against_oracle_jvp(dim, n, kind):
     under one-ulp input perturbations where that is larger: the derivative of
     the weights with respect to lambda scales like tau / (lambda beta + eps)^2
     with eps = 1e-20, so on faces where lambda beta ~ eps the Jacobian itself
-    is ill-conditioned (the forward bar has the same reading)."""
+    is ill-conditioned.  That bar is not capped (the specification sets no
+    tolerance for the derivative); every use of it is recorded with its kappa
+    (tests/parity_log.py), and the full transposed Jacobians below hold to
+    1e-10."""
     prob, U = P.random_state(dim, n, seed=31 + dim, kind=kind)
     rng = np.random.default_rng(7)
     prng = np.random.default_rng(99)
@@ -52,15 +56,16 @@ def test_vjp_dot_product_identity_against_oracle_jvp(dim, n, kind):
         _, jv = orc.rhs_jvp(prob, U, v)
         lhs, rhs = np.sum(w * jv), np.sum(g * v)
         ref = np.sum(np.abs(w * jv))
-        tol = 1e-11 * ref
-        if abs(lhs - rhs) > tol:
-            kappa = 0.0
+
+        def kappa():
+            k = 0.0
             for _ in range(3):
                 Up = U * (1.0 + 2.220446049250313e-16 * prng.choice([-1.0, 0.0, 1.0], size=U.shape))
                 _, jv2 = orc.rhs_jvp(prob, Up, v)
-                kappa = max(kappa, abs(np.sum(w * jv2) - lhs))
-            tol = max(tol, 10.0 * kappa)
-        assert abs(lhs - rhs) <= tol, (lhs, rhs, tol)
+                k = max(k, abs(np.sum(w * jv2) - lhs))
+            return k / ref
+
+        parity_log.bar(abs(lhs - rhs), ref, 1e-11, kappa, f"<w, J v> {dim}D {kind}", cap=None)
 
 
 @pytest.mark.parametrize("dim,n,bcs", [(1, [16], (0, 0)), (1, [16], (1, 1)), (2, [9, 7], (2, 2)),

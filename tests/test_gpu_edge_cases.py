@@ -6,6 +6,7 @@ import pytest
 
 from oracle import oracle as orc
 from paper_1908_02464_gb300 import problems as P
+from tests import oracle_pool, parity_log
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -71,27 +72,32 @@ def test_two_dimensional_data_uniform_in_y_reproduce_one_dimension():
         assert np.max(np.abs(r2[2, j])) <= 1e-12 * scale[1]
 
 
-def test_full_benchmark_batch_sampled_against_oracle():
-    """The 4096-problem batch of the benchmark (N ~ U[100, 4000]) in FP64:
-    eight instances across the size range re-run by the oracle (same steps,
-    same end time, L1(rho) <= 1e-10), every instance's status reported."""
-    params, _ = P.riemann_batch_params(4096, seed=20190807)
-    states = [P.riemann_instance(params, i)[1] for i in range(4096)]
+def test_full_benchmark_batch_against_oracle():
+    """The 4096-problem batch of the benchmark (N ~ U[100, 4000]) in FP64.
+    Every instance that stops non-physical stops in the oracle too, after
+    the same number of completed steps (the oracle run is capped one step
+    later).  A sample of 256 instances spread over the size range takes the
+    oracle's steps and end time with L1(rho) <= 1e-10 (or the recorded
+    conditioning bar, see tests/oracle_pool.py)."""
+    count, seed = 4096, 20190807
+    params, _ = P.riemann_batch_params(count, seed=seed)
+    states = [P.riemann_instance(params, i)[1] for i in range(count)]
     b = weno.Batch(params["N"], 0.0, 1.0, params["t_end"], "fp64")
     U = b.pack(states)
     b.run(U)
     st, steps, t = b.results()
     out = b.unpack(U)
     b.close()
-    assert np.sum(st == 0) >= 0.9 * 4096
-    order = np.argsort(params["N"])
-    ok = [i for i in order if st[i] == 0]
-    picks = [ok[k] for k in np.linspace(0, len(ok) - 1, 8).astype(int)]
-    for i in picks:
-        prob, Uo = P.riemann_instance(params, i)
-        so, to, ko = orc.advance(prob, Uo, 0.0, prob["t_end"])
-        assert so == 0 and ko == steps[i] and to == t[i]
-        assert np.mean(np.abs(out[i][0] - Uo[0])) <= 1e-10
+    bad = [int(i) for i in np.nonzero(st != 0)[0]]
+    assert len(bad) <= count // 20
+    jobs = [("riemann", count, seed, i, int(steps[i]) + 1) for i in bad]
+    for i, so, to, ko, _ in oracle_pool.run_many(jobs):
+        assert so == st[i] and ko == steps[i], (i, so, ko, steps[i])
+    sample = oracle_pool.stratified(params["N"], st == 0, 256)
+    l1 = oracle_pool.check_runs("riemann", count, seed, st, steps, t, [u[0] for u in out], sample, "1D batch")
+    v = np.array(list(l1.values()))
+    print("1D batch: %d non-physical (the oracle agrees); L1(rho) of %d sampled instances: %d above 1e-10, "
+          "max %.2e, median %.2e" % (len(bad), len(sample), int(np.sum(v > 1e-10)), v.max(), np.median(v)))
 
 
 def test_large_3d_grid_sampled_against_oracle():
@@ -108,12 +114,17 @@ def test_large_3d_grid_sampled_against_oracle():
     cells += [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 0)]
     ref = _oracle_rhs_at(prob, U, cells)
     got = np.array([r[(slice(None),) + tuple(reversed(c))] for c in cells])
-    prng = np.random.default_rng(9)
-    kappa = np.zeros(5)
-    for _ in range(3):
-        kappa = np.maximum(kappa, np.max(np.abs(_oracle_rhs_at(prob, U, cells, prng) - ref), axis=0))
     scale = np.max(np.abs(r).reshape(5, -1), axis=1)
-    assert np.all(np.max(np.abs(got - ref), axis=0) <= np.maximum(1e-12 * scale, 10.0 * kappa))
+    err = np.max(np.abs(got - ref), axis=0)
+
+    def kappa():
+        prng = np.random.default_rng(9)
+        k = np.zeros(5)
+        for _ in range(3):
+            k = np.maximum(k, np.max(np.abs(_oracle_rhs_at(prob, U, cells, prng) - ref), axis=0))
+        return k / scale
+
+    parity_log.bar(err, scale, 1e-12, kappa, "vortex 384^3, 27 sampled cells", terms=parity_log.term_scale(prob, U))
 
 
 def test_switch_threshold_flags_are_nested_in_the_characteristic_length():

@@ -21,6 +21,7 @@ import pytest
 
 from oracle import oracle as orc
 from paper_1908_02464_gb300 import problems as P
+from tests import parity_log
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -31,6 +32,12 @@ if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts t
 from paper_1908_02464_gb300 import weno  # noqa: E402
 
 RTOL64 = 1e-12
+# The developed Mach 2000 jet (Sec. 4.7, lambda read as 3600 sigma): on these
+# states the oracle itself moves by up to a few 1e-9 (relative) under one-ulp
+# input perturbations, i.e. its faces sit where the regularized weights are
+# ill-conditioned; the RHS comparisons at the segment restarts take a bar of
+# ten times that sensitivity, capped here instead of at the general 1e-9.
+JET_KAPPA_CAP = 1e-7
 
 
 def _gpu_rhs(prob, U, precision="fp64", t=0.0):
@@ -45,29 +52,38 @@ def _gpu_rhs(prob, U, precision="fp64", t=0.0):
     return out
 
 
-def _compare_rhs(prob, U, t=0.0, rtol=RTOL64, precision="fp64"):
+def _compare_rhs(prob, U, t=0.0, rtol=RTOL64, precision="fp64", label=None, strict=False,
+                 cap=parity_log.KAPPA_CAP):
+    """GPU RHS and face flags against the oracle's; returns the parity record
+    (tests/parity_log.py): the level of the bar that held, rel per variable,
+    kappa where measured, and the hybrid-flag mismatches (each within
+    FLAG_WINDOW of the threshold)."""
     ref, oflags, ratio = orc.rhs(prob, U, t, want_flags=True)
     got, gflags = _gpu_rhs(prob, U, precision, t)
     mism = np.nonzero(gflags != oflags)[0]
-    near = np.abs(ratio[mism] - 1.0) < 1e-9
-    assert np.all(near), f"{len(mism)} flag mismatches, ratios {ratio[mism][:5]}"
+    win = np.abs(ratio[mism] - 1.0)
+    assert np.all(win < parity_log.FLAG_WINDOW), f"{len(mism)} flag mismatches, ratios {ratio[mism][:5]}"
     nv = U.shape[0]
     scale = np.max(np.abs(ref).reshape(nv, -1), axis=1)
-    # a field whose reference RHS vanishes is measured on the largest field's scale
     scale = np.where(scale > 0.0, scale, max(float(scale.max()), 1e-300))
-    rel = np.max(np.abs(got - ref).reshape(nv, -1), axis=1) / scale
-    if len(mism) == 0 and np.all(rel <= rtol):
-        return rel, float(np.mean(oflags)), 0
-    # the oracle's own sensitivity to one-ulp input perturbations
-    rng = np.random.default_rng(12345)
-    kappa = np.zeros(nv)
-    for _ in range(3):
-        Up = U * (1.0 + 2.220446049250313e-16 * rng.choice([-1.0, 0.0, 1.0], size=U.shape))
-        rp = orc.rhs(prob, Up, t)
-        kappa = np.maximum(kappa, np.max(np.abs(rp - ref).reshape(nv, -1), axis=1) / scale)
-    tol = np.maximum(rtol, 10.0 * kappa)
-    assert np.all(rel <= tol), (rel, kappa)
-    return rel, float(np.mean(oflags)), len(mism)
+    err = np.max(np.abs(got - ref).reshape(nv, -1), axis=1)
+
+    def kappa():
+        # the oracle's own sensitivity to one-ulp input perturbations
+        rng = np.random.default_rng(12345)
+        k = np.zeros(nv)
+        for _ in range(3):
+            Up = U * (1.0 + 2.220446049250313e-16 * rng.choice([-1.0, 0.0, 1.0], size=U.shape))
+            rp = orc.rhs(prob, Up, t)
+            k = np.maximum(k, np.max(np.abs(rp - ref).reshape(nv, -1), axis=1) / scale)
+        return k
+
+    rec = parity_log.bar(err, scale, rtol, kappa, label or prob.get("name", "rhs"),
+                         terms=parity_log.term_scale(prob, U), n_flag_mismatch=len(mism),
+                         max_flag_window=float(win.max()) if len(mism) else 0.0, n_faces=int(oflags.size),
+                         strict=strict, cap=cap)
+    rec["weno_face_fraction"] = float(1.0 - np.mean(oflags))
+    return rec
 
 
 # ------------------------------------------------------------------ RHS
@@ -76,27 +92,27 @@ def _compare_rhs(prob, U, t=0.0, rtol=RTOL64, precision="fp64"):
 @pytest.mark.parametrize("n", [[300], [7], [129]])
 def test_rhs_parity_1d(kind, n):
     prob, U = P.random_state(1, n, seed=100 + n[0], kind=kind)
-    _compare_rhs(prob, U)
+    _compare_rhs(prob, U, strict=kind == "smooth")
 
 
 @pytest.mark.parametrize("kind", ["smooth", "mixed", "jumps"])
 @pytest.mark.parametrize("n", [[150, 37], [64, 8], [33, 70]])
 def test_rhs_parity_2d(kind, n):
     prob, U = P.random_state(2, n, seed=200 + n[0], kind=kind)
-    _compare_rhs(prob, U)
+    _compare_rhs(prob, U, strict=kind == "smooth")
 
 
 @pytest.mark.parametrize("kind", ["smooth", "mixed", "jumps"])
 def test_rhs_parity_3d(kind):
     prob, U = P.random_state(3, [70, 20, 13], seed=300, kind=kind)
-    _compare_rhs(prob, U)
+    _compare_rhs(prob, U, strict=kind == "smooth")
 
 
 def test_rhs_parity_hybrid_off():
     prob, U = P.random_state(2, [40, 24], seed=5, kind="mixed")
     prob["hybrid"] = 0
-    rel, frac, _ = _compare_rhs(prob, U)
-    assert frac == 0.0
+    rec = _compare_rhs(prob, U)
+    assert rec["weno_face_fraction"] == 1.0
 
 
 @pytest.mark.parametrize("weights", ["is", "wang", "linear"])
@@ -196,7 +212,7 @@ def test_mach2000_jet_full_run():
     errs, terrs = [], []
     steps = 0
     while t < prob["t_end"]:
-        _compare_rhs(prob, Uo, t=t)
+        _compare_rhs(prob, Uo, t=t, cap=JET_KAPPA_CAP)
         s.set_state(Uo, t)
         kg = s.advance(prob["t_end"], max_steps=100)
         V, tg = s.get_state()
@@ -215,7 +231,7 @@ def test_mach2000_jet_full_run():
     g = prob["gamma"]
     p = (g - 1.0) * (Uo[3] - 0.5 * (Uo[1] ** 2 + Uo[2] ** 2) / Uo[0])
     assert Uo[0].min() > 0.0 and p.min() > 0.0
-    _compare_rhs(prob, Uo, t=t)
+    _compare_rhs(prob, Uo, t=t, cap=JET_KAPPA_CAP)
 
 
 def test_mach2000_jet_mixed_precision_reports_the_failure():
@@ -252,7 +268,50 @@ def test_rhs_parity_boundaries():
 def test_rhs_parity_double_mach_full_size():
     """The 2048 x 512 double Mach reflection at the size the benchmark times."""
     prob, U = P.double_mach(2048, 512)
-    _compare_rhs(prob, U, t=0.0)
+    _compare_rhs(prob, U, t=0.0, label="double Mach 2048x512, t = 0")
+
+
+def test_double_mach_developed_full_size_rhs_and_step():
+    """The state the benchmark times: 2048 x 512 advanced on the GPU from the
+    initial condition to t = 0.05 (Mach stem, slip line, reflected shocks).
+    On that exact state the GPU RHS equals the oracle's (1e-12 per variable,
+    or the logged conditioning bar), and one GPU RK3 step equals one oracle
+    step: dt to rounding, the state to 1e-12 per variable, L1(rho) <= 1e-10."""
+    prob, U0 = P.double_mach(2048, 512)
+    s = weno.Solver(prob, "fp64")
+    s.set_state(U0)
+    s.advance(0.05)
+    U, t = s.get_state()
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    assert abs(t - 0.05) < 1e-15
+    rec = _compare_rhs(prob, U, t=t, label="double Mach 2048x512, developed t = 0.05")
+    assert rec["weno_face_fraction"] > 0.01        # shocks, stem and slip line present
+
+    s.set_state(U, t)
+    dt_g = s.step(1.0)
+    V, tg = s.get_state()
+    s.close()
+    Uo = U.copy()
+    st, to, dt_o = orc.step(prob, Uo, t, 1.0)
+    assert st == 0
+    # the CFL step from the largest wave-speed sum, against that sum evaluated
+    # in extended precision: both sides within rounding of the exact value
+    q = U.astype(np.longdouble)
+    g = np.longdouble(1.4)
+    u, v = q[1] / q[0], q[2] / q[0]
+    p = (g - 1) * (q[3] - (q[1] * u + q[2] * v) / 2)
+    c = np.sqrt(g * p / q[0])
+    smax = np.max((np.abs(u) + c) * 512 + (np.abs(v) + c) * 512)
+    ex = float(np.longdouble(0.5) / smax)
+    dev = {"gpu": abs(dt_g - ex) / ex, "oracle": abs(dt_o - ex) / ex, "gpu_vs_oracle": abs(dt_g - dt_o) / dt_o}
+    print("developed double Mach: CFL step relative deviations", dev)
+    assert dev["gpu"] <= 1e-13 and dev["oracle"] <= 1e-13, dev
+    assert abs(tg - to) <= 1e-13 * to
+    scale = np.max(np.abs(Uo).reshape(4, -1), axis=1)
+    err = np.max(np.abs(V - Uo).reshape(4, -1), axis=1)
+    parity_log.bar(err, scale, 1e-12, lambda: np.full(4, np.inf), "double Mach 2048x512, one RK3 step from t = 0.05",
+                   strict=True)
+    assert np.mean(np.abs(V[0] - Uo[0])) <= 1e-10
 
 
 def _oracle_rhs_at(prob, U, cells, rng=None):
@@ -294,13 +353,19 @@ def test_rhs_parity_vortex_3d_full_size_sampled():
     g = np.array([got[(slice(None),) + tuple(reversed(c))] for c in cells])
     scale = np.max(np.abs(got).reshape(5, -1), axis=1)
     err = np.max(np.abs(g - ref), axis=0)
-    # p = 100 makes the momentum and energy fluxes ~100 while their divergence
-    # is O(0.1): the oracle's own one-ulp sensitivity sets the bar there
-    prng = np.random.default_rng(7)
-    kappa = np.zeros(5)
-    for _ in range(3):
-        kappa = np.maximum(kappa, np.max(np.abs(_oracle_rhs_at(prob, U, cells, prng) - ref), axis=0))
-    assert np.all(err <= np.maximum(RTOL64 * scale, 10.0 * kappa)), (err, kappa, scale)
+
+    # the density RHS vanishes analytically (divergence-free velocity at
+    # rho = 1) and p = 100 makes the momentum and energy fluxes ~100 while
+    # their divergence is O(0.1): the flux-term scale sets the bar there
+    def kappa():
+        prng = np.random.default_rng(7)
+        k = np.zeros(5)
+        for _ in range(3):
+            k = np.maximum(k, np.max(np.abs(_oracle_rhs_at(prob, U, cells, prng) - ref), axis=0))
+        return k / scale
+
+    parity_log.bar(err, scale, RTOL64, kappa, "vortex 256^3, 64 sampled cells",
+                   terms=parity_log.term_scale(prob, U))
 
 
 # ------------------------------------------------------------------ steps
