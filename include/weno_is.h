@@ -292,6 +292,46 @@ weno_status weno_batch_weno_face_count(weno_batch* batch, unsigned long long* co
 void weno_batch_destroy(weno_batch* batch);
 const char* weno_batch_last_error(const weno_batch* batch);
 
+/* ------------------------------------------------------------------------
+ * Batched 2D problems (many independent 2D boxes of uneven sizes).
+ * Instance i is a 2D Euler problem on [lo_x[i], hi_x[i]] x [lo_y[i], hi_y[i]]
+ * with nx[i] x ny[i] cells, advanced from t = 0 to t_end[i] with its own CFL
+ * step (dt = CFL / max (|u| + c)/dx + (|v| + c)/dy, Sec. 4) by the same
+ * dimension-by-dimension scheme as weno_step (Sec. 2.4, Eq. goveq5), in one
+ * persistent launch replayed from a CUDA graph: every CTA takes the next
+ * instance from a work queue ordered by nx ny max(nx, ny) (cells x steps),
+ * largest first, and runs its whole RK3 loop on its own.  Each stage is the
+ * y sweep (flux divergence into an accumulator) followed by the x sweep
+ * (its divergence plus the RK3 combination), as in the grid solver, whose
+ * results the batch reproduces bit for bit.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int count;              /* number of instances (>= 1)                      */
+    const int* nx;          /* host [count]: cells along x (>= 3)              */
+    const int* ny;          /* host [count]: cells along y (>= 3)              */
+    const double* lo_x;     /* host [count]                                    */
+    const double* hi_x;
+    const double* lo_y;
+    const double* hi_y;
+    const double* t_end;    /* host [count]: end time of each instance         */
+    int bc_lo[2], bc_hi[2]; /* per direction (x, y): WENO_BC_TRANSMISSIVE, _REFLECT or _PERIODIC */
+    int max_steps;          /* per-instance step limit, 0 = none               */
+} weno_batch2d_desc;
+
+/* Create a 2D batch: the returned handle takes weno_batch_run, _results,
+ * _autotune, _set_config (variants 0..2: x / y tiles of 4x31 / 8x15 and 2x63
+ * / 4x31 on 128 threads, 2x31 / 4x15 on 64 threads), _weno_face_count and
+ * _destroy like a 1D batch.  States are one device array holding the
+ * instances back to back, instance i as [4][ny[i]][nx[i]] (rho, rho u, rho v,
+ * E; x fastest) starting at element 4 sum_{j<i} nx[j] ny[j] (double for
+ * WENO_FP64, float otherwise).  Allocates four work arrays of the batch's
+ * size.  Errors: WENO_ERR_INVALID_ARG for an empty batch, nx or ny < 3,
+ * hi <= lo, negative t_end, other boundary codes, unpaired periodic
+ * boundaries or an unknown precision; WENO_ERR_UNSUPPORTED for global
+ * Lax-Friedrichs splitting; WENO_ERR_CUDA if allocation fails. */
+weno_status weno_batch2d_create(const weno_batch2d_desc* desc, const weno_params* params, void* stream,
+                                weno_batch** out);
+
 /* One-call form: create, run, collect per-instance status (host array of
  * count ints, may be NULL), destroy. */
 weno_status weno_batch_solve(const weno_batch_desc* desc, const weno_params* params, void* stream, void* U_dev,

@@ -1,7 +1,9 @@
 """In-tree build of ``libweno_is.so`` for sm_103a with nvcc.
 
-The four translation units (host API and one per arithmetic) compile in
-parallel; the shared library lands in ``paper_1908_02464_gb300/_build``.
+The seven translation units (the host API, one per arithmetic of the grid
+solver, the allocation-free totals, the 1D and the 2D batched solvers)
+compile in parallel; the shared library lands in
+``paper_1908_02464_gb300/_build``.
 """
 from __future__ import annotations
 
@@ -15,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libweno_is.so")
-UNITS = ["weno_api", "weno_f64", "weno_f32", "weno_mixed", "weno_noalloc", "weno_batch"]
-HEADERS = ["weno_device.cuh", "weno_kernels.cuh", "weno_launch.cuh", "weno_adjoint.cuh"]
+UNITS = ["weno_api", "weno_f64", "weno_f32", "weno_mixed", "weno_noalloc", "weno_batch", "weno_batch2d"]
+HEADERS = ["weno_device.cuh", "weno_kernels.cuh", "weno_launch.cuh", "weno_adjoint.cuh", "weno_batch.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

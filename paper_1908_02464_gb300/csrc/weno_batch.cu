@@ -1,6 +1,7 @@
-// Batched 1D solver: many independent Euler problems of uneven sizes, each
+// Batched solver: many independent Euler problems of uneven sizes, each
 // advanced to its own end time with its own CFL step, in one persistent
-// launch replayed from a CUDA graph.
+// launch replayed from a CUDA graph.  This file holds the 1D kernel and the
+// host object shared with the 2D kernel of weno_batch2d.cu.
 //
 // Each CTA pulls an instance from a work queue (instances ordered largest
 // first, so the tail of the schedule holds the small ones), copies it into
@@ -21,34 +22,10 @@
 #include <vector>
 
 #include "../../include/weno_is.h"
+#include "weno_batch.cuh"
 #include "weno_kernels.cuh"
 
 namespace wis {
-
-struct BatchArgs {
-    int count;
-    const int* order;        // instance ids, largest first
-    const int* n;            // cells per instance
-    const long long* off;    // offset of instance i in U ([3][n_i] interior)
-    const long long* goff;   // offset of instance i in each work array ([3][n_i + 6])
-    const double* dx;
-    const double* t_end;
-    void* U;
-    void* work0;
-    void* work1;
-    void* work2;
-    int* status;             // per instance: 0 ok, WENO_ERR_NONPHYSICAL
-    long long* steps;
-    double* t_out;
-    unsigned int* head;      // work-queue counter (reset before each launch)
-    unsigned long long* weno_count;
-    int max_steps;
-    const int* trial_caps;   // autotuner trial runs: step cap per instance (null otherwise)
-    int write_back;          // 0: trial run, the caller's states are not touched
-    double gamma, cfl, eps, c_lambda, C_thr, L_char;
-    int alpha_thr, hybrid, bc_lo, bc_hi;
-    int wmode, split;
-};
 
 template <int V> struct BatchTile;
 template <> struct BatchTile<0> { static constexpr int SEG = 127, NT = 128; };
@@ -202,6 +179,7 @@ cudaError_t batch_launch(const BatchArgs& b, int blocks, cudaStream_t s)
 using wis::BatchArgs;
 
 struct weno_batch {
+    int dim = 1;   // 1: [3][n] instances (k_batch); 2: [4][ny][nx] instances (k_batch2d)
     int count = 0, prec = 0, dev = 0, nsm = 1;
     size_t esz = 8;
     weno_params p;
@@ -215,14 +193,17 @@ struct weno_batch {
     long long* goff = nullptr;
     double* dx = nullptr;
     double* t_end = nullptr;
-    void* work[3] = {nullptr, nullptr, nullptr};
+    int* ny = nullptr;        // 2D
+    double* dy = nullptr;     // 2D
+    int bc_lo_y = 0, bc_hi_y = 0;
+    void* work[4] = {nullptr, nullptr, nullptr, nullptr};   // the fourth: 2D accumulator
     int* status = nullptr;
     long long* steps = nullptr;
     double* t_out = nullptr;
     unsigned int* head = nullptr;
     unsigned long long* wcount = nullptr;
     int* trial_caps = nullptr;
-    std::vector<int> n_host;
+    std::vector<int> n_host;      // steps grow with this size: n (1D), max(nx, ny) (2D)
     int variant = 0;
     int blocks = 0;
     cudaGraphExec_t graph = nullptr;
@@ -241,9 +222,10 @@ static std::string g_batch_err;
         }                                                                                   \
     } while (0)
 
-static cudaError_t batch_dispatch_config(int prec, int v, int* bps, size_t* smem)
+static cudaError_t batch_dispatch_config(int dim, int prec, int v, int* bps, size_t* smem)
 {
     using namespace wis;
+    if (dim == 2) return batch2d_config(prec, v, bps, smem);
     if (prec == WENO_FP64) {
         if (v == 1) return batch_config<double, false, 1>(bps, smem);
         if (v == 2) return batch_config<double, false, 2>(bps, smem);
@@ -255,9 +237,10 @@ static cudaError_t batch_dispatch_config(int prec, int v, int* bps, size_t* smem
     return ex ? batch_config<float, true, 0>(bps, smem) : batch_config<float, false, 0>(bps, smem);
 }
 
-static cudaError_t batch_dispatch_launch(int prec, int v, const BatchArgs& b, int blocks, cudaStream_t s)
+static cudaError_t batch_dispatch_launch(int dim, int prec, int v, const BatchArgs& b, int blocks, cudaStream_t s)
 {
     using namespace wis;
+    if (dim == 2) return batch2d_launch(prec, v, b, blocks, s);
     if (prec == WENO_FP64) {
         if (v == 1) return batch_launch<double, false, 1>(b, blocks, s);
         if (v == 2) return batch_launch<double, false, 2>(b, blocks, s);
@@ -287,6 +270,9 @@ static BatchArgs batch_args(weno_batch* bt, void* U, int max_steps, int write_ba
     b.C_thr = bt->p.C_thr; b.L_char = bt->p.L_char; b.alpha_thr = bt->p.alpha_thr; b.hybrid = bt->p.hybrid;
     b.bc_lo = bt->bc_lo; b.bc_hi = bt->bc_hi;
     b.wmode = bt->p.weights; b.split = bt->p.splitting;
+    b.ny = bt->ny; b.dy = bt->dy;
+    b.bc_lo_y = bt->bc_lo_y; b.bc_hi_y = bt->bc_hi_y;
+    b.work3 = bt->work[3];
     return b;
 }
 
@@ -294,7 +280,7 @@ static weno_status set_variant(weno_batch* bt, int v, int blocks_per_sm_cap)
 {
     int bps = 0;
     size_t smem = 0;
-    BCK(batch_dispatch_config(bt->prec, v, &bps, &smem));
+    BCK(batch_dispatch_config(bt->dim, bt->prec, v, &bps, &smem));
     if (bps < 1) { bt->err = "batch kernel cannot be resident"; return WENO_ERR_CUDA; }
     if (blocks_per_sm_cap > 0 && bps > blocks_per_sm_cap) bps = blocks_per_sm_cap;
     bt->variant = v;
@@ -314,14 +300,15 @@ static cudaError_t enqueue_run(weno_batch* bt, void* U, int max_steps, int write
     if (e != cudaSuccess) return e;
     BatchArgs b = batch_args(bt, U, max_steps, write_back);
     b.trial_caps = trial_caps;
-    return batch_dispatch_launch(bt->prec, bt->variant, b, bt->blocks, s);
+    return batch_dispatch_launch(bt->dim, bt->prec, bt->variant, b, bt->blocks, s);
 }
 
 static void batch_free(weno_batch* bt)
 {
     if (bt->graph) cudaGraphExecDestroy(bt->graph);
     void* ptrs[] = {bt->order, bt->n, bt->off, bt->goff, bt->dx, bt->t_end, bt->work[0], bt->work[1],
-                    bt->work[2], bt->status, bt->steps, bt->t_out, bt->head, bt->wcount, bt->trial_caps};
+                    bt->work[2], bt->work[3], bt->status, bt->steps, bt->t_out, bt->head, bt->wcount,
+                    bt->trial_caps, bt->ny, bt->dy};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (bt->cap) cudaStreamDestroy(bt->cap);
@@ -433,6 +420,125 @@ weno_status weno_batch_create(const weno_batch_desc* d, const weno_params* param
     return WENO_OK;
 }
 
+weno_status weno_batch2d_create(const weno_batch2d_desc* d, const weno_params* params, void* stream,
+                                weno_batch** out)
+{
+    if (out) *out = nullptr;
+    if (!d || !params || !out || d->count < 1 || !d->nx || !d->ny || !d->lo_x || !d->hi_x || !d->lo_y ||
+        !d->hi_y || !d->t_end) {
+        g_batch_err = "invalid 2D batch description";
+        return WENO_ERR_INVALID_ARG;
+    }
+    if (params->precision < WENO_FP64 || params->precision > WENO_MIXED || d->max_steps < 0 ||
+        params->weights < 0 || params->weights > 3 || params->splitting < 0 || params->splitting > 2) {
+        g_batch_err = "invalid precision, weights, splitting or max_steps";
+        return WENO_ERR_INVALID_ARG;
+    }
+    if (params->splitting == 1) {
+        g_batch_err = "global Lax-Friedrichs splitting is not available for batches (use LLF or Roe)";
+        return WENO_ERR_UNSUPPORTED;
+    }
+    for (int a = 0; a < 2; ++a) {
+        for (int s = 0; s < 2; ++s) {
+            const int bc = s == 0 ? d->bc_lo[a] : d->bc_hi[a];
+            if (bc != WENO_BC_TRANSMISSIVE && bc != WENO_BC_REFLECT && bc != WENO_BC_PERIODIC) {
+                g_batch_err = "batched problems take transmissive, reflecting or periodic boundaries";
+                return WENO_ERR_INVALID_ARG;
+            }
+        }
+        if ((d->bc_lo[a] == WENO_BC_PERIODIC) != (d->bc_hi[a] == WENO_BC_PERIODIC)) {
+            g_batch_err = "periodic boundaries must be paired";
+            return WENO_ERR_INVALID_ARG;
+        }
+    }
+    const int cnt = d->count;
+    std::vector<long long> off(cnt);
+    std::vector<double> dx(cnt), dy(cnt), tend(cnt), work(cnt);
+    std::vector<int> lin(cnt);
+    long long tc = 0;
+    for (int i = 0; i < cnt; ++i) {
+        if (d->nx[i] < 3 || d->ny[i] < 3 || !(d->hi_x[i] > d->lo_x[i]) || !(d->hi_y[i] > d->lo_y[i]) ||
+            !(d->t_end[i] >= 0.0)) {
+            g_batch_err = "instance with nx or ny < 3, hi <= lo or negative t_end";
+            return WENO_ERR_INVALID_ARG;
+        }
+        off[i] = tc;
+        tc += 4LL * d->nx[i] * d->ny[i];
+        dx[i] = (d->hi_x[i] - d->lo_x[i]) / d->nx[i];
+        dy[i] = (d->hi_y[i] - d->lo_y[i]) / d->ny[i];
+        tend[i] = d->t_end[i];
+        lin[i] = std::max(d->nx[i], d->ny[i]);
+        // work of a run ~ cells x steps, and the steps grow with the finer spacing
+        work[i] = (double)d->nx[i] * d->ny[i] * lin[i];
+    }
+    // schedule: most work first
+    std::vector<int> order(cnt);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+
+    weno_batch* bt = new (std::nothrow) weno_batch();
+    if (!bt) { g_batch_err = "out of host memory"; return WENO_ERR_CUDA; }
+    bt->dim = 2;
+    bt->count = cnt;
+    bt->p = *params;
+    bt->prec = params->precision;
+    bt->esz = bt->prec == WENO_FP64 ? sizeof(double) : sizeof(float);
+    bt->bc_lo = d->bc_lo[0];
+    bt->bc_hi = d->bc_hi[0];
+    bt->bc_lo_y = d->bc_lo[1];
+    bt->bc_hi_y = d->bc_hi[1];
+    bt->max_steps = d->max_steps > 0 ? d->max_steps : 0x7fffffff;
+    bt->stream = (cudaStream_t)stream;
+    bt->total_cells = tc / 4;
+    bt->total_ghosted = tc;
+    cudaError_t e = cudaGetDevice(&bt->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&bt->nsm, cudaDevAttrMultiProcessorCount, bt->dev);
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc((void**)&bt->order, sizeof(int) * cnt);
+    alloc((void**)&bt->n, sizeof(int) * cnt);
+    alloc((void**)&bt->ny, sizeof(int) * cnt);
+    alloc((void**)&bt->off, sizeof(long long) * cnt);
+    alloc((void**)&bt->goff, sizeof(long long) * cnt);
+    alloc((void**)&bt->dx, sizeof(double) * cnt);
+    alloc((void**)&bt->dy, sizeof(double) * cnt);
+    alloc((void**)&bt->t_end, sizeof(double) * cnt);
+    for (int k = 0; k < 4; ++k) alloc(&bt->work[k], bt->esz * (size_t)tc);
+    alloc((void**)&bt->status, sizeof(int) * cnt);
+    alloc((void**)&bt->steps, sizeof(long long) * cnt);
+    alloc((void**)&bt->t_out, sizeof(double) * cnt);
+    alloc((void**)&bt->head, sizeof(unsigned int));
+    alloc((void**)&bt->wcount, sizeof(unsigned long long));
+    alloc((void**)&bt->trial_caps, sizeof(int) * cnt);
+    bt->n_host = lin;
+    if (e == cudaSuccess) e = cudaMemcpy(bt->order, order.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->n, d->nx, sizeof(int) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->ny, d->ny, sizeof(int) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->off, off.data(), sizeof(long long) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->goff, off.data(), sizeof(long long) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->dx, dx.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->dy, dy.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bt->t_end, tend.data(), sizeof(double) * cnt, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(bt->wcount, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        g_batch_err = std::string("weno_batch2d_create: ") + cudaGetErrorString(e);
+        batch_free(bt);
+        delete bt;
+        return WENO_ERR_CUDA;
+    }
+    weno_status st = set_variant(bt, 0, 0);
+    if (st != WENO_OK) {
+        g_batch_err = bt->err;
+        batch_free(bt);
+        delete bt;
+        return st;
+    }
+    *out = bt;
+    return WENO_OK;
+}
+
 void weno_batch_destroy(weno_batch* bt)
 {
     if (!bt) return;
@@ -504,7 +610,7 @@ weno_status weno_batch_weno_face_count(weno_batch* bt, unsigned long long* count
 weno_status weno_batch_set_config(weno_batch* bt, int variant, int blocks_per_sm, int* blocks)
 {
     if (!bt) return WENO_ERR_INVALID_ARG;
-    if (variant < 0 || variant >= wis::kBatchVariants || blocks_per_sm < 0) {
+    if (variant < 0 || variant >= (bt->dim == 2 ? wis::kBatch2Variants : wis::kBatchVariants) || blocks_per_sm < 0) {
         bt->err = "set_config: variant must be 0, 1 or 2 and blocks_per_sm >= 0";
         return WENO_ERR_INVALID_ARG;
     }
@@ -529,7 +635,7 @@ weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_ste
     // have spread, and trials from the initial jumps rank the configurations
     // unlike full runs do (they favour small tiles that lose on developed
     // solutions)
-    const size_t sbytes = (size_t)bt->total_cells * 3 * bt->esz;
+    const size_t sbytes = (size_t)bt->total_cells * (bt->dim + 2) * bt->esz;
     void* Us = nullptr;
     double* t_half = nullptr;
     BCK(cudaMalloc(&Us, sbytes));
@@ -548,7 +654,7 @@ weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_ste
     if (ce == cudaSuccess) {
         BatchArgs b = batch_args(bt, Us, bt->max_steps, 1);
         b.t_end = t_half;
-        ce = batch_dispatch_launch(bt->prec, bt->variant, b, bt->blocks, bt->stream);
+        ce = batch_dispatch_launch(bt->dim, bt->prec, bt->variant, b, bt->blocks, bt->stream);
     }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(bt->stream);
     cudaFree(t_half);
@@ -566,7 +672,8 @@ weno_status weno_batch_autotune(weno_batch* bt, const void* U_dev, int trial_ste
     int best_v = bt->variant, best_cap = 0;
     const int caps[3] = {0, 4, 2};   // 0 = as many CTAs per SM as fit
     weno_status st = WENO_OK;
-    for (int v = 0; v < wis::kBatchVariants && st == WENO_OK; ++v) {
+    const int nvariants = bt->dim == 2 ? wis::kBatch2Variants : wis::kBatchVariants;
+    for (int v = 0; v < nvariants && st == WENO_OK; ++v) {
         for (int c = 0; c < 3 && st == WENO_OK; ++c) {
             st = set_variant(bt, v, caps[c]);
             if (st != WENO_OK) break;

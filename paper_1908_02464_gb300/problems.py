@@ -12,8 +12,8 @@ Grids are cell-centred: x_i = lo + (i + 1/2) dx.
 
 Problems follow Sec. 4 of the paper (Sod and Lax shock tubes, 123 problem,
 two blast waves, Shu-Osher, double Mach reflection) and the derived
-workloads: smooth periodic advection, a batch of random Riemann problems and
-a periodic 3D vortex.
+workloads: smooth periodic advection, batches of random 1D Riemann problems
+and of random 2D cylindrical explosions, and a periodic 3D vortex.
 """
 from __future__ import annotations
 
@@ -268,6 +268,59 @@ def riemann_batch_params(count: int = 4096, seed: int = 20190807, gamma: float =
         T[i] = 0.2 / max(abs(ul) + cl, abs(ur) + cr)
         i += 1
     return dict(N=N, WL=WL, WR=WR, t_end=T, gamma=gamma), redraws
+
+
+def explosion_batch_params(count: int = 4096, seed: int = 20190808, gamma: float = 1.4, n_lo: int = 16,
+                           n_hi: int = 64, h: float = 1.0 / 64.0):
+    """Random cylindrical explosions and implosions (2D Riemann problems of
+    a disc at rest in a gas at rest) in boxes of uneven sizes.
+
+    Instance i: NX ~ U{n_lo..n_hi} and NY ~ U{n_lo..n_hi} square cells of
+    side h on [0, NX h] x [0, NY h]; a disc of radius r ~ U[0.15, 0.35]
+    min(Lx, Ly) centred at (U[0.4, 0.6] Lx, U[0.4, 0.6] Ly); rho and p
+    log-uniform in [0.1, 10] inside and outside, redrawn (from the same
+    stream) while the density ratio across the disc edge exceeds 20 -- the
+    scheme has no positivity limiter, and larger ratios on the staircase edge
+    of a disc drive the first step to a negative pressure; transmissive
+    boundaries; t_end = 0.2 min(Lx, Ly) / max(c_in, c_out).
+    Returns a dict of arrays and the number of redraws."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    NX = np.zeros(count, dtype=np.int64); NY = np.zeros(count, dtype=np.int64)
+    r = np.zeros(count); cx = np.zeros(count); cy = np.zeros(count)
+    rho = np.zeros((count, 2)); p = np.zeros((count, 2))     # inside, outside
+    redraws = 0
+    i = 0
+    while i < count:
+        nx, ny = (int(v) for v in rng.integers(n_lo, n_hi + 1, size=2))
+        fr, fx, fy = rng.uniform(0.15, 0.35), rng.uniform(0.4, 0.6), rng.uniform(0.4, 0.6)
+        ri, ro, pi, po = np.exp(rng.uniform(np.log(0.1), np.log(10.0), size=4))
+        if max(ri / ro, ro / ri) > 20.0:
+            redraws += 1
+            continue
+        NX[i], NY[i] = nx, ny
+        L = min(nx, ny) * h
+        r[i], cx[i], cy[i] = fr * L, fx * nx * h, fy * ny * h
+        rho[i] = (ri, ro); p[i] = (pi, po)
+        i += 1
+    c = np.sqrt(gamma * p / rho)
+    T = 0.2 * np.minimum(NX, NY) * h / c.max(axis=1)
+    return dict(NX=NX, NY=NY, h=h, r=r, cx=cx, cy=cy, rho=rho, p=p, t_end=T, gamma=gamma), redraws
+
+
+def explosion_instance(params: dict, i: int):
+    """Problem description and initial state [4][NY][NX] of instance i of an
+    explosion batch (transmissive boundaries)."""
+    nx, ny, h = int(params["NX"][i]), int(params["NY"][i]), params["h"]
+    g = params["gamma"]
+    x = centers(0.0, nx * h, nx)[None, :]
+    y = centers(0.0, ny * h, ny)[:, None]
+    inside = (x - params["cx"][i]) ** 2 + (y - params["cy"][i]) ** 2 < params["r"][i] ** 2
+    rho = np.where(inside, params["rho"][i, 0], params["rho"][i, 1])
+    p = np.where(inside, params["p"][i, 0], params["p"][i, 1])
+    z = np.zeros((ny, nx))
+    prob = _base(2, [nx, ny], [0.0, 0.0], [nx * h, ny * h], [BC_TRANSMISSIVE] * 2, [BC_TRANSMISSIVE] * 2,
+                 float(params["t_end"][i]), f"explosion_{i}", gamma=g)
+    return prob, prim_to_cons(g, rho, [z, z], p)
 
 
 def riemann_instance(params: dict, i: int):

@@ -53,6 +53,14 @@ class weno_batch_desc(ctypes.Structure):
                 ("bc_lo", ctypes.c_int), ("bc_hi", ctypes.c_int), ("max_steps", ctypes.c_int)]
 
 
+class weno_batch2d_desc(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("nx", ctypes.POINTER(ctypes.c_int)), ("ny", ctypes.POINTER(ctypes.c_int)),
+                ("lo_x", ctypes.POINTER(ctypes.c_double)), ("hi_x", ctypes.POINTER(ctypes.c_double)),
+                ("lo_y", ctypes.POINTER(ctypes.c_double)), ("hi_y", ctypes.POINTER(ctypes.c_double)),
+                ("t_end", ctypes.POINTER(ctypes.c_double)), ("bc_lo", ctypes.c_int * 2), ("bc_hi", ctypes.c_int * 2),
+                ("max_steps", ctypes.c_int)]
+
+
 _vp = ctypes.c_void_p
 _ip = ctypes.c_int
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -80,6 +88,8 @@ SIGNATURES = {
     "weno_autotune": (ctypes.c_int, [_vp, _ip, ctypes.POINTER(_ip)]),
     "weno_batch_create": (ctypes.c_int, [ctypes.POINTER(weno_batch_desc), ctypes.POINTER(weno_params), _vp,
                                          ctypes.POINTER(_vp)]),
+    "weno_batch2d_create": (ctypes.c_int, [ctypes.POINTER(weno_batch2d_desc), ctypes.POINTER(weno_params), _vp,
+                                           ctypes.POINTER(_vp)]),
     "weno_batch_run": (ctypes.c_int, [_vp, _vp]),
     "weno_batch_results": (ctypes.c_int, [_vp, ctypes.POINTER(_ip), ctypes.POINTER(ctypes.c_longlong), _dp]),
     "weno_batch_weno_face_count": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong), _ip]),
@@ -430,6 +440,29 @@ def weno_batch_create(N, lo, hi, t_end, params: weno_params, bc_lo=0, bc_hi=0, m
     return b.value
 
 
+def weno_batch2d_create(NX, NY, lo, hi, t_end, params: weno_params, bc_lo=(0, 0), bc_hi=(0, 0), max_steps=0,
+                        stream: int = 0) -> int:
+    """lo, hi: (x, y) pairs, one for all instances or one per instance."""
+    NX = np.ascontiguousarray(NX, dtype=np.int32)
+    NY = np.ascontiguousarray(NY, dtype=np.int32)
+    lo = np.broadcast_to(np.asarray(lo, dtype=np.float64), NX.shape + (2,))
+    hi = np.broadcast_to(np.asarray(hi, dtype=np.float64), NX.shape + (2,))
+    cols = [np.ascontiguousarray(a[:, k]) for a in (lo, hi) for k in (0, 1)]
+    te = np.ascontiguousarray(t_end, dtype=np.float64)
+    d = weno_batch2d_desc()
+    d.count = int(NX.size)
+    d.nx = NX.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    d.ny = NY.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    d.lo_x, d.lo_y, d.hi_x, d.hi_y = (c.ctypes.data_as(_dp) for c in cols)
+    d.t_end = te.ctypes.data_as(_dp)
+    for k in range(2):
+        d.bc_lo[k], d.bc_hi[k] = int(bc_lo[k]), int(bc_hi[k])
+    d.max_steps = int(max_steps)
+    b = _vp()
+    _bcheck(load().weno_batch2d_create(ctypes.byref(d), ctypes.byref(params), _vp(stream or None), ctypes.byref(b)))
+    return b.value
+
+
 def weno_batch_run(batch: int, U_dev) -> None:
     _bcheck(load().weno_batch_run(_vp(batch), _vp(_ptr(U_dev))), _vp(batch))
 
@@ -525,6 +558,33 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Batch2D(Batch):
+    """Many independent 2D Euler problems (instance i: NY[i] x NX[i] cells,
+    state [4][NY[i]][NX[i]]) solved by one persistent launch."""
+
+    def __init__(self, NX, NY, lo, hi, t_end, precision: str = "fp64", gamma: float = 1.4, bc_lo=(0, 0),
+                 bc_hi=(0, 0), max_steps: int = 0, stream=None, **params):
+        import torch
+        self.NX = np.asarray(NX, dtype=np.int64)
+        self.NY = np.asarray(NY, dtype=np.int64)
+        self.count = int(self.NX.size)
+        self.offsets = np.concatenate([[0], np.cumsum(4 * self.NX * self.NY)])
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        p = weno_default_params()
+        p.gamma = gamma
+        for k, v in params.items():
+            setattr(p, k, v)
+        p.precision = PRECISIONS[precision]
+        s = stream.cuda_stream if stream is not None else 0
+        self.handle = weno_batch2d_create(self.NX, self.NY, lo, hi, t_end, p, bc_lo, bc_hi, max_steps, s)
+
+    def unpack(self, U_dev):
+        h = U_dev.double().cpu().numpy()
+        return [h[self.offsets[i]:self.offsets[i + 1]].reshape(4, int(self.NY[i]), int(self.NX[i]))
+                for i in range(self.count)]
 
 
 # ----------------------------------------------------------------- autograd
