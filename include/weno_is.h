@@ -202,14 +202,15 @@ weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t fl
  * the fastest for this context.  Shapes (variant: lines x cells per CTA):
  * 0: 2x63, 1: 8x15, 2: 4x31, 3: 1x127, 4: 1x95, 5: flat, 123 consecutive
  * faces of the line-after-line face sequence (a tile may end one line and
- * start the next; lines shorter than 122 cells take variant 3).  Defaults:
+ * start the next; lines shorter than 122 cells take variant 3), 6: flat
+ * with 251 faces on 256 threads (lines shorter than 250 take 3).  Defaults:
  * FP64 5 in every direction; FP32 and mixed 3 along x, 1 across.
  * variants[3] (if not NULL) receives the choice per direction.
  * The state is not changed; the step graphs are rebuilt on next use.
  * Synchronizes. */
 weno_status weno_autotune(weno_ctx* ctx, int reps, int* variants);
 
-/* Pin the tile shape of every sweep direction (variants[d] in 0..5, see
+/* Pin the tile shape of every sweep direction (variants[d] in 0..6, see
  * weno_autotune; ignored in 1D).  Results do not depend on the tile shape:
  * every face is computed by the same arithmetic.  WENO_ERR_INVALID_ARG for
  * an unknown variant. */

@@ -222,6 +222,51 @@ __device__ __forceinline__ void back_proj_add(const Roe<T, DIM>& r, const T* w, 
     out[LAST] += e + eshear;
 }
 
+// Row v of sum_s R[v][s] w[s] (Eq. reconstruction2), with the same FP64
+// operations for every v so that neighbouring lanes holding different rows
+// do not diverge: the row's entries are picked by selects (integer pipe)
+// and summed over the fields in their order,
+//   R[v][u-c] = base - cn, R[v][u] = ent, R[v][t] = sh_t, R[v][u+c] = base + cn,
+// with (base, cn, ent, sh_t) = (1, 0, 1, 0) for v = 0 (mass),
+// (u_k, c [k = n], u_k, [k = t]) for v = 1 + k (momentum k) and
+// (H, u_n c, q^2/2, u_t) for v = NV - 1 (energy).
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ T back_proj_row(const Roe<T, DIM>& r, const T* w, int v)
+{
+    constexpr int LAST = DIM + 1;
+    const T unc = r.u[DIR] * r.c;
+    T base = T(1), cn = T(0), ent = T(1);
+    T sh[DIM > 1 ? DIM - 1 : 1];
+#pragma unroll
+    for (int t = 0; t < DIM - 1; ++t) sh[t] = T(0);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        if (v == 1 + k) {
+            base = r.u[k];
+            ent = r.u[k];
+            cn = k == DIR ? r.c : T(0);
+        }
+    }
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        if (k == DIR) continue;
+        if (v == 1 + k) sh[s] = T(1);
+        if (v == LAST) sh[s] = r.u[k];
+        ++s;
+    }
+    if (v == LAST) {
+        base = r.H;
+        cn = unc;
+        ent = r.hq2;
+    }
+    T acc = (base - cn) * w[0];
+    acc = fmaT(ent, w[1], acc);
+#pragma unroll
+    for (int t = 0; t < DIM - 1; ++t) acc = fmaT(sh[t], w[2 + t], acc);
+    return fmaT(base + cn, w[LAST], acc);
+}
+
 // out += sum_s R^s alpha^s w^s with w = L dU and the entropy and shear fields
 // sharing one speed a0 (the LLF, global LF and Roe splittings all do): since
 // R w = R L dU = dU, the sum is a0 dU + (am - a0) w_0 R^{u-c} + (ap - a0)

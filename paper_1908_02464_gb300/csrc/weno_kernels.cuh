@@ -169,7 +169,7 @@ __device__ __forceinline__ void stage_cell(const SweepArgs& a, const T* Ug, long
 
 template <typename T, int DIM>
 struct FaceRec {
-    // record of a queued WENO face: Roe state, lambda^s, LLF speeds
+    // record of a queued WENO face: Roe state, detector, LLF speeds
     static constexpr int NV = DIM + 2;
     static constexpr int U = 0;               // u[DIM]
     static constexpr int C = DIM;
@@ -177,16 +177,19 @@ struct FaceRec {
     static constexpr int H = DIM + 2;
     static constexpr int B1 = DIM + 3;
     static constexpr int HQ2 = DIM + 4;
-    static constexpr int LAM = DIM + 5;       // lambda^s = c (dv^s / rho~)^2, NV entries
-    static constexpr int AM = LAM + NV;       // alpha^{u-c}
-    static constexpr int A0 = AM + 1;         // alpha^{u}, shear
-    static constexpr int AP = AM + 2;         // alpha^{u+c}
+    static constexpr int W = DIM + 5;         // 60 dv^s (Eq. eq28 without the 1/60), NV entries
+    static constexpr int AM = W + NV;         // alpha^{u-c} / 2
+    static constexpr int A0 = AM + 1;         // alpha^{u} / 2, shear
+    static constexpr int AP = AM + 2;         // alpha^{u+c} / 2
     static constexpr int MASK = AM + 3;       // per-field smooth bits (per-field hybrid)
-    static constexpr int NR = AM + 4;
+    static constexpr int IRT2 = AM + 4;       // 1 / rho~^2
+    static constexpr int NR = AM + 5;
 };
 
-// WENO faces are processed in chunks of QC queued faces.
-template <int DIM> struct Chunk { static constexpr int QC = 16; };
+// WENO faces are processed in chunks of QC queued faces: 16, or one eighth
+// of the tile's faces for tiles of 256 faces and more (in 2D a chunk then
+// gives one reconstruction, per face, field and sign, to every thread).
+template <int NFACE> struct Chunk { static constexpr int QC = NFACE >= 256 ? NFACE / 8 : 16; };
 
 template <typename T, int DIM, int LINES, int SEG, bool FLAT = false>
 struct SweepSmem {
@@ -199,7 +202,7 @@ struct SweepSmem {
     static constexpr int NQ = CellLayout<DIM>::NQ;
     static constexpr int NV = DIM + 2;
     static constexpr int NR = FaceRec<T, DIM>::NR;
-    static constexpr int QC = Chunk<DIM>::QC;
+    static constexpr int QC = Chunk<NFACE>::QC;
     static constexpr size_t bytes =
         sizeof(T) * ((size_t)NQ * NCELL + (size_t)NV * NFACE + (size_t)NR * NFACE +
                      (size_t)QC * NV * 2 * 6 + (size_t)QC * NV * 2) +
@@ -453,10 +456,12 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
                 fr[FR::H * NFACE + f] = r.H;
                 fr[FR::B1 * NFACE + f] = r.b1;
                 fr[FR::HQ2 * NFACE + f] = r.hq2;
-                // Eq. eq27, eq29: lambda^s = c (dv^s / rho~)^2 = c w_s^2 / (3600 rho~^2)
-                const T irt2 = Ar<T>::rcp(r.rt * r.rt);
+                // the regularization parameters of Eq. eq27, eq29 are formed
+                // in phase 2 from w and 1 / rho~^2 (few lanes of this warp
+                // take this branch)
 #pragma unroll
-                for (int s = 0; s < NV; ++s) fr[(FR::LAM + s) * NFACE + f] = lam_scale * (w[s] * w[s]) * irt2;
+                for (int s = 0; s < NV; ++s) fr[(FR::W + s) * NFACE + f] = w[s];
+                fr[FR::IRT2 * NFACE + f] = Ar<T>::rcp_f(r.rt * r.rt);
                 // half splitting speeds (Eq. flxuspliting: f+- = (g +- alpha v) / 2)
                 fr[FR::AM * NFACE + f] = T(0.5) * am;
                 fr[FR::A0 * NFACE + f] = T(0.5) * a0;
@@ -534,31 +539,36 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
                 const T al = s == 0 ? am : (s == NV - 1 ? ap : a0);
                 const T h = T(0.5) * wg[s];
                 const T k = al * wv[s];   // al holds alpha / 2
+                // f+ in stencil order j-2 .. j+3, f- mirrored (j+3 .. j-2), so
+                // that both signs take the same call in 2b (neighbouring lanes
+                // hold the two signs and would otherwise diverge)
                 fpm[((q * NV + s) * 2 + 0) * 6 + m] = h + k;
-                fpm[((q * NV + s) * 2 + 1) * 6 + m] = h - k;
+                fpm[((q * NV + s) * 2 + 1) * 6 + (5 - m)] = h - k;
             }
         }
         __syncthreads();
         // 2b: one reconstruction per (face, field, sign): Eq. eq6, eq11, eq18,
-        //     eq8-r; the minus part on the mirrored stencil j+3 .. j-1
+        //     eq8-r; the minus part on the mirrored stencil j+3 .. j-1 (stored
+        //     mirrored by 2a)
         for (int it = threadIdx.x; it < qc * NV * 2; it += NT) {
             const int q = it / (2 * NV);
             const int rem = it - q * (2 * NV);
             const int s = rem >> 1, sg = rem & 1;
             const int f = queue[q0 + q];
-            const T lam = fr[(FR::LAM + s) * NFACE + f];
+            // Eq. eq27, eq29: lambda^s = c (dv^s / rho~)^2 = c w_s^2 / (3600 rho~^2)
+            const T ws = fr[(FR::W + s) * NFACE + f];
+            const T lam = lam_scale * (ws * ws) * fr[FR::IRT2 * NFACE + f];
             // per-field hybrid: the linear scheme for a smooth field
             const int fm_bits = (int)fr[FR::MASK * NFACE + f];
             const int wm = (fm_bits >> s) & 1 ? W_LINEAR : a.wmode;
             const T* v = fpm + ((q * NV + s) * 2 + sg) * 6;
-            T out;
-            if (sg == 0) out = recon<T>(v[0], v[1], v[2], v[3], v[4], lam, eps, wm);
-            else out = recon<T>(v[5], v[4], v[3], v[2], v[1], lam, eps, wm);
-            res[(q * NV + s) * 2 + sg] = out;
+            res[(q * NV + s) * 2 + sg] = recon<T>(v[0], v[1], v[2], v[3], v[4], lam, eps, wm);
         }
         __syncthreads();
-        // 2c: Eq. reconstruction1 and the back-projection Eq. reconstruction2
-        for (int q = threadIdx.x; q < qc; q += NT) {
+        // 2c: Eq. reconstruction1 and the back-projection Eq. reconstruction2,
+        //     one work item per (face, conserved variable)
+        for (int it = threadIdx.x; it < qc * NV; it += NT) {
+            const int q = it / NV, v = it - (it / NV) * NV;
             const int f = queue[q0 + q];
             Roe<T, DIM> r;
 #pragma unroll
@@ -566,15 +576,10 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             r.c = fr[FR::C * NFACE + f];
             r.H = fr[FR::H * NFACE + f];
             r.hq2 = fr[FR::HQ2 * NFACE + f];
-            T wch[NV], Fo[NV];
+            T wch[NV];
 #pragma unroll
-            for (int s = 0; s < NV; ++s) {
-                wch[s] = res[(q * NV + s) * 2] + res[(q * NV + s) * 2 + 1];
-                Fo[s] = T(0);
-            }
-            back_proj_add<T, DIM, DIR>(r, wch, Fo);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) fh[v * NFACE + f] = T(60) * Fo[v];
+            for (int s = 0; s < NV; ++s) wch[s] = res[(q * NV + s) * 2] + res[(q * NV + s) * 2 + 1];
+            fh[v * NFACE + f] = T(60) * back_proj_row<T, DIM, DIR>(r, wch, v);
         }
     }
     __syncthreads();

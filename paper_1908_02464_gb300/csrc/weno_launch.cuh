@@ -28,7 +28,10 @@ namespace wis {
 //             one line stages exactly 128 cells, one per thread, where 128
 //             faces would leave a second round of 5 cells; lines shorter
 //             than 122 cells take variant 3 instead
-constexpr int kTileVariants = 6;
+//   6 flat256 the flat tile with 251 faces on 256 threads (two CTAs per SM):
+//             half the partly filled last warp per face, twice the WENO
+//             faces per tile; lines shorter than 250 cells take variant 3
+constexpr int kTileVariants = 7;
 template <int V> struct Tile;
 template <> struct Tile<0> { static constexpr int LINES = 2, SEG = 63, NT = 128; static constexpr bool FLAT = false; };
 template <> struct Tile<1> { static constexpr int LINES = 8, SEG = 15, NT = 128; static constexpr bool FLAT = false; };
@@ -36,6 +39,7 @@ template <> struct Tile<2> { static constexpr int LINES = 4, SEG = 31, NT = 128;
 template <> struct Tile<3> { static constexpr int LINES = 1, SEG = 127, NT = 128; static constexpr bool FLAT = false; };
 template <> struct Tile<4> { static constexpr int LINES = 1, SEG = 95, NT = 96; static constexpr bool FLAT = false; };
 template <> struct Tile<5> { static constexpr int LINES = 1, SEG = 122, NT = 128; static constexpr bool FLAT = true; };
+template <> struct Tile<6> { static constexpr int LINES = 1, SEG = 250, NT = 256; static constexpr bool FLAT = true; };
 struct Tile1D { static constexpr int LINES = 1, SEG = 127, NT = 128; static constexpr bool FLAT = false; };
 
 template <typename T, int DIM, int DIR, bool EXACTDET, typename TL>
@@ -75,6 +79,10 @@ cudaError_t launch_sweep_v(int variant, const SweepArgs& a, cudaStream_t s)
     if (variant == 4) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<4>>(a, s);
     if (variant == 5) {
         if (a.n[DIR] >= Tile<5>::SEG) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<5>>(a, s);
+        return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<3>>(a, s);
+    }
+    if (variant == 6) {
+        if (a.n[DIR] >= Tile<6>::SEG) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<6>>(a, s);
         return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<3>>(a, s);
     }
     return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<0>>(a, s);

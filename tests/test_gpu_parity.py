@@ -454,13 +454,16 @@ def _variant_cases():
     cases = []
     # 122 cells: the shortest lines that take flat tiles, so that a tile
     # starting late in one line covers the whole of the next line's start
-    for dim, n in ((2, [150, 37]), (2, [300, 140]), (2, [122, 121]), (3, [40, 23, 19]), (3, [130, 9, 128])):
+    # 250: the shortest lines that take the 251-face flat tiles
+    for dim, n in ((2, [150, 37]), (2, [300, 140]), (2, [122, 121]), (2, [250, 263]), (3, [40, 23, 19]),
+                   (3, [130, 9, 128])):
         cases.append(P.random_state(dim, n, seed=77, kind="mixed"))
     # non-periodic boundaries on lines long enough for flat tiles: double Mach
     # (inflow, wall, moving shock), the jet inflow, and a 3D box with
     # reflecting and transmissive faces
     prob, U = P.double_mach(200, 130)
     cases.append((prob, U))
+    cases.append(P.double_mach(520, 260))
     cases.append(P.mach2000_jet(160, 40))
     cases.append(_box3d_walls())
     return cases
@@ -484,14 +487,14 @@ def test_rhs_parity_3d_walls_flat_tiles():
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_tile_variants_give_bitwise_identical_results(precision):
     """Every face is computed by the same arithmetic whatever the tiling,
-    including flat tiles (variant 5) whose pieces span two lines, and the
-    fallback to variant 3 on lines shorter than 122 cells."""
+    including flat tiles (variants 5 and 6) whose pieces span two lines, and
+    the fallback to variant 3 on lines shorter than 122 (250) cells."""
     for prob, U in _variant_cases():
         if precision != "fp64" and prob["name"] == "mach2000_jet":
             continue   # FP32 cannot represent the jet's pressure (see the jet tests)
         dim = prob["dim"]
         outs = []
-        for v in range(6):
+        for v in range(7):
             s = weno.Solver(prob, precision)
             s.set_tiles([v] * dim)
             Ud = torch.from_numpy(U).cuda()
@@ -514,7 +517,7 @@ def test_autotune_keeps_state_and_results():
     s.advance(0.002)
     V0, t0 = s.get_state()
     v = s.autotune(2)
-    assert all(0 <= x < 6 for x in v)
+    assert all(0 <= x < 7 for x in v)
     V1, t1 = s.get_state()
     assert t1 == t0 and np.array_equal(V0, V1)
     s.close()
