@@ -404,8 +404,11 @@ def test_fifth_order_convergence_on_the_gpu():
     t = 0.5 with dt = 0.5 dx^(5/3) so that the RK3 error stays below the
     spatial one: the CUDA path's L1 error of density against the exact
     translate falls at fifth order (Sec. 2: optimal weights on smooth data),
-    and at N = 40 its final state is the oracle's."""
-    ns = [20, 40, 80, 160, 320]
+    and at N = 40 its final state is the oracle's.  N = 20..640: fifth order
+    up to 320 cells; at 640 cells the truncation error (about 3e-13) meets the
+    rounding accumulated over about 15,000 FP64 steps, so there the error is
+    only required to keep falling (order 4) and to stay below 1e-12."""
+    ns = [20, 40, 80, 160, 320, 640]
     errs = []
     for n in ns:
         prob, U = P.density_wave(n)
@@ -427,7 +430,8 @@ def test_fifth_order_convergence_on_the_gpu():
             assert st == 0 and to == T
             assert np.max(np.abs(V - Uo)) <= 1e-12 * np.max(np.abs(Uo))
     order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-    assert np.all(order[1:] > 4.7), (errs, order)
+    assert np.all(order[1:4] > 4.7), (errs, order)
+    assert order[4] > 3.5 and errs[5] < 1e-12, (errs, order)
 
 
 def test_double_mach_steps_parity():

@@ -482,9 +482,14 @@ def test_lax_and_123_run_and_track_exact():
 
 @pytest.mark.parametrize("which", ["advection", "density_wave"])
 def test_fifth_order_convergence(which):
+    """u_t + u_x = 0 with u0 = sin(pi x) on [-1, 1] (and the Euler density
+    wave) at N = 20..640 (scalar) / 20..320 (Euler), dt = 0.5 dx^(5/3): fifth
+    order over every doubling up to 320 cells.  At 640 cells the scalar error
+    (about 2e-12) meets the rounding accumulated over 15,000 steps, so the
+    last doubling is held to order 4.5."""
     fn = P.advection_sine if which == "advection" else P.density_wave
     errs = []
-    ns = [20, 40, 80, 160]
+    ns = [20, 40, 80, 160, 320, 640] if which == "advection" else [20, 40, 80, 160, 320]
     for n in ns:
         prob, U = fn(n)
         st, t, k = orc.advance(prob, U, 0.0, prob["t_end"])
@@ -493,7 +498,8 @@ def test_fifth_order_convergence(which):
         ex = np.sin(np.pi * (x - 0.5)) if which == "advection" else 1 + 0.2 * np.sin(np.pi * (x - 0.5))
         errs.append(np.mean(np.abs(U[0] - ex)))
     order = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-    assert np.all(order[1:] > 4.7), order
+    assert np.all(order[1:4] > 4.7), order
+    assert np.all(order[4:] > 4.5), order
 
 
 def test_nonphysical_state_reported_and_restored():
