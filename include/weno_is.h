@@ -136,9 +136,13 @@ weno_status weno_get_state(weno_ctx* ctx, void* U, int on_device, double* t);
 
 /* Semi-discrete right-hand side dU/dt (Eq. goveq5 summed over directions) of
  * the interior-only device array U_dev, with ghost cells filled at time t.
- * dUdt_dev: interior-only device array of the same shape, overwritten.  The
- * context's own state is not touched.  Asynchronous on the context's
- * stream; returns WENO_ERR_CUDA if a launch fails. */
+ * dUdt_dev: interior-only device array of the same shape, overwritten; it
+ * must not overlap U_dev (WENO_ERR_INVALID_ARG if the two are the same
+ * array).  The sweeps read U_dev and write dUdt_dev in place, with no copy
+ * into the context's padded layout (the ghost cells are computed from the
+ * boundary conditions while the tiles are staged).  The context's own state
+ * is not touched.  Asynchronous on the context's stream; returns
+ * WENO_ERR_CUDA if a launch fails. */
 weno_status weno_rhs(weno_ctx* ctx, const void* U_dev, void* dUdt_dev, double t);
 
 /* Vector-Jacobian product of the semi-discrete operator (the adjoint of

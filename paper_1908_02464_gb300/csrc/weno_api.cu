@@ -525,10 +525,34 @@ static weno_status ensure_rhs_bufs(weno_ctx* ctx)
     return WENO_OK;
 }
 
-// sweeps of a stand-alone RHS at time t on rhs_in -> rhs_out (flags optional)
-static weno_status issue_rhs(weno_ctx* ctx, double t, uint8_t* flags)
+// sweeps of a stand-alone RHS at time t on U -> out (flags optional), both in
+// the caller's interior-only layout [nvar][nz][ny][nx]: the tiles compute the
+// ghost cells while staging and read interior cells only, so they take the
+// caller's arrays with plain strides, and the accumulator of the earlier
+// directions uses the same strides
+static void plain_strides(const weno_ctx* ctx, long long& sy, long long& sz, long long& sv)
 {
-    if (ctx->p.splitting == wis::SPLIT_LF) CK(issue_lf(ctx, ctx->rhs_in, 3, nullptr, ctx->stream));
+    sy = ctx->n[0];
+    sz = (long long)ctx->n[0] * ctx->n[1];
+    sv = sz * ctx->n[2];
+}
+
+static weno_status issue_rhs(weno_ctx* ctx, const void* U, void* out, double t, uint8_t* flags)
+{
+    long long sy, sz, sv;
+    plain_strides(ctx, sy, sz, sv);
+    if (ctx->p.splitting == wis::SPLIT_LF) {
+        unsigned long long* ag = ctx->alpha_g + 3 * 9;
+        CK(cudaMemsetAsync(ag, 0, 9 * sizeof(unsigned long long), ctx->stream));
+        wis::CflArgs ca;
+        std::memset(&ca, 0, sizeof(ca));
+        ca.U = U;
+        for (int k = 0; k < 3; ++k) ca.n[k] = ctx->n[k];
+        ca.sy = sy; ca.sz = sz; ca.sv = sv; ca.off0 = 0;
+        ca.gamma = ctx->p.gamma;
+        CK(ctx->prec == WENO_FP64 ? wis::lf_f64(ctx->dim, ca, ag, ctx->nsm, ctx->stream)
+                                  : wis::lf_f32(ctx->dim, ca, ag, ctx->nsm, ctx->stream));
+    }
     // flags of direction d start after the faces of the directions before it
     long long foff[3] = {0, 0, 0};
     for (int d = 1; d < ctx->dim; ++d) {
@@ -541,14 +565,15 @@ static weno_status issue_rhs(weno_ctx* ctx, double t, uint8_t* flags)
     for (int i = 0; i < ctx->dim; ++i) {
         const int d = ctx->dim - 1 - i;
         wis::SweepArgs a = sweep_args(ctx, d);
-        a.U = ctx->rhs_in;
+        a.sy = sy; a.sz = sz; a.sv = sv; a.off0 = 0;
+        a.U = U;
         a.xs_fixed = wis::dmr_shock_x(t);
         a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
         if (flags) a.flags = flags + foff[d];
         if (d == 0) {
             a.mode = wis::MODE_RHS;
             a.acc = ctx->dim > 1 ? ctx->acc : nullptr;
-            a.out = ctx->rhs_out;
+            a.out = out;
         } else {
             a.mode = i == 0 ? wis::MODE_ACC_SET : wis::MODE_ACC_ADD;
             a.acc = ctx->acc;
@@ -560,14 +585,8 @@ static weno_status issue_rhs(weno_ctx* ctx, double t, uint8_t* flags)
 
 weno_status weno_rhs(weno_ctx* ctx, const void* U_dev, void* dUdt_dev, double t)
 {
-    if (!ctx || !U_dev || !dUdt_dev) return WENO_ERR_INVALID_ARG;
-    weno_status st = ensure_rhs_bufs(ctx);
-    if (st != WENO_OK) return st;
-    CK(do_pack(ctx, U_dev, ctx->rhs_in, 1, ctx->stream));
-    st = issue_rhs(ctx, t, nullptr);
-    if (st != WENO_OK) return st;
-    CK(do_pack(ctx, ctx->rhs_out, dUdt_dev, 0, ctx->stream));
-    return WENO_OK;
+    if (!ctx || !U_dev || !dUdt_dev || U_dev == dUdt_dev) return WENO_ERR_INVALID_ARG;
+    return issue_rhs(ctx, U_dev, dUdt_dev, t, nullptr);
 }
 
 weno_status weno_face_flags(weno_ctx* ctx, const void* U_dev, double t, uint8_t* flags_dev)
@@ -575,8 +594,8 @@ weno_status weno_face_flags(weno_ctx* ctx, const void* U_dev, double t, uint8_t*
     if (!ctx || !U_dev || !flags_dev) return WENO_ERR_INVALID_ARG;
     weno_status st = ensure_rhs_bufs(ctx);
     if (st != WENO_OK) return st;
-    CK(do_pack(ctx, U_dev, ctx->rhs_in, 1, ctx->stream));
-    return issue_rhs(ctx, t, flags_dev);
+    // the fluxes of this evaluation go to a scratch array the caller never sees
+    return issue_rhs(ctx, U_dev, ctx->rhs_out, t, flags_dev);
 }
 
 weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, void* gU_dev, double t)

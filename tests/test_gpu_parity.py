@@ -265,6 +265,26 @@ def test_rhs_parity_boundaries():
     _compare_rhs(prob, U, t=0.013)
 
 
+def test_rhs_reads_and_writes_the_callers_arrays():
+    """weno_rhs takes the caller's interior-only arrays with plain strides (no
+    copy into the padded layout): results do not depend on what the output
+    array held, repeated calls agree bitwise, and an output that is the input
+    array is rejected."""
+    prob, U = P.random_state(2, [70, 33], seed=9, kind="mixed")
+    s = weno.Solver(prob, "fp64")
+    Ud = torch.from_numpy(U).cuda()
+    a = torch.full_like(Ud, float("nan"))
+    b = torch.full_like(Ud, 7.0)
+    s.rhs(Ud, 0.0, out=a)
+    s.rhs(Ud, 0.0, out=b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and bool(torch.isfinite(a).all())
+    with pytest.raises(weno.WenoError) as e:
+        weno.weno_rhs(s.ctx, Ud, Ud, 0.0)
+    assert e.value.status == weno.WENO_ERR_INVALID_ARG
+    s.close()
+
+
 def test_rhs_parity_double_mach_full_size():
     """The 2048 x 512 double Mach reflection at the size the benchmark times."""
     prob, U = P.double_mach(2048, 512)
