@@ -635,6 +635,16 @@ def vortex3d_rhs_vjp(args) -> dict:
         ms_rhs = timeit(lambda: s.rhs(Ud, 0.0, out=r))
         wf = s.weno_faces() / 3.0   # per RHS evaluation (three timed evaluations)
         ms_vjp = timeit(lambda: s.rhs_vjp(Ud, wd, 0.0, out=g))
+        # one more call of each inside NVTX ranges, for launch lists
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(f"rhs_{prec}")
+        s.rhs(Ud, 0.0, out=r)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.nvtx.range_push(f"vjp_{prec}")
+        s.rhs_vjp(Ud, wd, 0.0, out=g)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         s.set_state(Ud)
         s.autotune(2)
         s.enqueue_steps(10.0, 1)
