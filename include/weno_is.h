@@ -155,11 +155,14 @@ weno_status weno_rhs(weno_ctx* ctx, const void* U_dev, void* dUdt_dev, double t)
  * detector, projections, nonlinear weights); nothing is stored between
  * calls.  Ghost-cell contributions are mapped back through the boundary
  * conditions (fixed inflow states receive none).  U_dev, w_dev, gU_dev:
- * interior-only device arrays of the state's shape and element type.
- * Deterministic (no atomics).  Asynchronous; WENO_ERR_CUDA if a launch or
- * an allocation of the backward buffers fails; WENO_ERR_UNSUPPORTED unless
- * the context uses the regularized weights with LLF splitting and hybrid
- * 0 or 1. */
+ * interior-only device arrays of the state's shape and element type, read
+ * and written in place (the tiles compute U's ghost cells while staging;
+ * the cotangent is zero on ghost cells); gU_dev must not overlap U_dev or
+ * w_dev (WENO_ERR_INVALID_ARG if it is one of them).  Deterministic (no
+ * atomics).  Asynchronous; WENO_ERR_CUDA if a launch or the first call's
+ * allocation of the per-line ghost-gradient buffer fails;
+ * WENO_ERR_UNSUPPORTED unless the context uses the regularized weights with
+ * LLF splitting and hybrid 0 or 1. */
 weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, void* gU_dev, double t);
 
 /* Per-face hybrid flags of U_dev at time t: 1 where the linear upwind scheme

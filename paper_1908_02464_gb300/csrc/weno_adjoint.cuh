@@ -270,9 +270,9 @@ __device__ __forceinline__ void recon_adj(T a, T b, T c, T d, T e, T lam, T eps,
 }
 
 struct VjpArgs {
-    const void* U;      // ghosted state, ghosts filled
-    const void* W;      // ghosted cotangent, ghosts zero
-    void* G;            // ghosted gradient accumulator (interior written)
+    const void* U;      // state, interior only (the caller's array)
+    const void* W;      // cotangent, interior only
+    void* G;            // gradient, interior only (written / accumulated)
     void* ghost;        // [line][6][NV] gradients of ghost cells
     int accumulate;     // 0: G = ..., 1: G += ...
     int n[3];
@@ -280,6 +280,10 @@ struct VjpArgs {
     double inv_dx, eps_h, gamma, eps, c_lambda;
     double slim;   // 60 sqrt(eps_h), as in the forward sweep
     int hybrid;
+    // boundary conditions of this direction, for the ghost cells computed
+    // while staging (the fields stage_cell reads: bc_lo, bc_hi, bc_state,
+    // lo0, dx0, lo1, dx1, tm = null, xs_fixed)
+    SweepArgs bc;
 };
 
 // A tile is LINES grid lines x SEG cells along the sweep, one thread per
@@ -312,10 +316,22 @@ struct VjpSmem {
         sizeof(T) * ((size_t)NQ * LNC + (size_t)NV * LNC + (size_t)LNF * NFB) + sizeof(int) * (size_t)LNF;
 };
 
+// Residency of the adjoint kernel: the per-face reverse pass needs more than
+// 255 registers, which leaves 8 warps per SM.  FP64 is held to 4 CTAs per SM
+// by shared memory anyway and keeps its FP64 pipe 79-85% busy; FP32 code
+// needs more warps to hide its latencies, so its register count is capped at
+// 128 (8 CTAs of the 64-thread x tiles, 2 of the 256-thread y/z tiles, which
+// their shared memory allows) at the cost of spills: the 256^3 FP32 VJP went
+// from 10.0 to 7.2 ms (same-GPU A/B, same result).
+template <typename T, int NT> struct VjpMinBlocks {
+    static constexpr int value = sizeof(T) == 4 ? (NT == 64 ? 8 : 2) : 1;
+};
+
 // one direction of the VJP: tile = LINES grid lines x SEG cells; shared
 // arrays hold position p of line l at p * LINES + l
 template <typename T, int DIM, int DIR>
-__global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT) k_vjp(VjpArgs a)
+__global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpTile<T, DIM, DIR>::NT>::value)
+    k_vjp(VjpArgs a)
 {
     using CL = CellLayout<DIM>;
     using SM = VjpSmem<T, DIM, DIR>;
@@ -346,15 +362,21 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT) k_vjp(VjpArgs a)
     const T* Wg = reinterpret_cast<const T*>(a.W);
     const T gamma = T(a.gamma);
 
-    // stage cells c0-5 .. c0+SEG+4 that exist (-3 .. nd+2)
+    // stage cells c0-5 .. c0+SEG+4 that exist (-3 .. nd+2); ghost cells come
+    // from the boundary conditions, and the cotangent is zero on them
     for (int idx = threadIdx.x; idx < LNC; idx += NT) {
         const int p = idx / LINES, l = idx - (idx / LINES) * LINES;
         const int cell = c0 - 5 + p;
         if (l < nlx && cell >= -3 && cell <= nd + 2) {
-            const long long g = base0 + l + (long long)cell * sd;
+            // in-plane index of the line for the boundary conditions: the row
+            // for x sweeps, the column for y and z sweeps
+            const int line = DIR == 0 ? j : ix0 + l;
             T U[NV];
+            stage_cell<T, DIM, DIR>(a.bc, Ug, base0 + l, line, cell, nd, U);
+            const bool inside = cell >= 0 && cell < nd;
+            const long long g = base0 + l + (long long)cell * sd;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) { U[v] = Ug[g + v * a.sv]; wq[v * LNC + idx] = Wg[g + v * a.sv]; }
+            for (int v = 0; v < NV; ++v) wq[v * LNC + idx] = inside ? Wg[g + v * a.sv] : T(0);
             T q[NQ];
             cell_prepare<T, DIM, DIR>(U, gamma, q);
 #pragma unroll

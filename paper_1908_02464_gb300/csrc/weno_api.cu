@@ -600,18 +600,11 @@ weno_status weno_face_flags(weno_ctx* ctx, const void* U_dev, double t, uint8_t*
 
 weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, void* gU_dev, double t)
 {
-    if (!ctx || !U_dev || !w_dev || !gU_dev) return WENO_ERR_INVALID_ARG;
+    if (!ctx || !U_dev || !w_dev || !gU_dev || gU_dev == U_dev || gU_dev == w_dev) return WENO_ERR_INVALID_ARG;
     if (ctx->p.weights != 0 || ctx->p.splitting != wis::SPLIT_LLF || ctx->p.hybrid == 2) {
         ctx->err = "the adjoint is implemented for the regularized weights with LLF splitting and the "
                    "per-face hybrid switch";
         return WENO_ERR_UNSUPPORTED;
-    }
-    weno_status st = ensure_rhs_bufs(ctx);
-    if (st != WENO_OK) return st;
-    const size_t bytes = ctx->buf_elems * ctx->esz;
-    if (!ctx->vjp_w) {
-        CK(cudaMalloc(&ctx->vjp_w, bytes));
-        CK(cudaMemsetAsync(ctx->vjp_w, 0, bytes, ctx->stream));
     }
     if (!ctx->vjp_ghost) {
         long long lines = 0;
@@ -623,34 +616,35 @@ weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, vo
         }
         CK(cudaMalloc(&ctx->vjp_ghost, (size_t)lines * 6 * ctx->nv * ctx->esz));
     }
-    CK(do_pack(ctx, U_dev, ctx->rhs_in, 1, ctx->stream));
-    CK(do_pack(ctx, w_dev, ctx->vjp_w, 1, ctx->stream));
-    for (int d = 0; d < ctx->dim; ++d) {
-        wis::GhostArgs ga = ghost_args(ctx, ctx->rhs_in, d);
-        ga.t_fixed = t;
-        CK(do_ghost(ctx, ga, ctx->stream));
-    }
+    // the caller's interior-only arrays with plain strides: the tiles compute
+    // the ghost cells of U from the boundary conditions while staging
+    long long sy, sz, sv;
+    plain_strides(ctx, sy, sz, sv);
     const bool f64 = ctx->prec == WENO_FP64;
     for (int d = 0; d < ctx->dim; ++d) {
         wis::VjpArgs a;
         std::memset(&a, 0, sizeof(a));
-        a.U = ctx->rhs_in;
-        a.W = ctx->vjp_w;
-        a.G = ctx->rhs_out;
+        a.U = U_dev;
+        a.W = w_dev;
+        a.G = gU_dev;
         a.ghost = ctx->vjp_ghost;
         a.accumulate = d > 0;
         for (int k = 0; k < 3; ++k) a.n[k] = ctx->n[k];
-        a.sy = ctx->sy; a.sz = ctx->sz; a.sv = ctx->sv; a.off0 = ctx->off0;
+        a.sy = sy; a.sz = sz; a.sv = sv; a.off0 = 0;
         a.inv_dx = ctx->inv_dx[d];
         a.eps_h = ctx->eps_h[d];
         a.slim = std::sqrt(3600.0 * a.eps_h);
         a.gamma = ctx->p.gamma; a.eps = ctx->p.eps; a.c_lambda = ctx->p.c_lambda; a.hybrid = ctx->p.hybrid;
+        a.bc = sweep_args(ctx, d);
+        a.bc.sy = sy; a.bc.sz = sz; a.bc.sv = sv; a.bc.off0 = 0;
+        a.bc.tm = nullptr;
+        a.bc.xs_fixed = wis::dmr_shock_x(t);
         CK(f64 ? wis::vjp_f64(ctx->dim, d, a, ctx->stream) : wis::vjp_f32(ctx->dim, d, a, ctx->stream));
-        wis::GhostArgs ga = ghost_args(ctx, ctx->rhs_out, d);
-        CK(f64 ? wis::ghost_adj_f64(ctx->dim, ga, ctx->vjp_ghost, ctx->rhs_out, ctx->stream)
-               : wis::ghost_adj_f32(ctx->dim, ga, ctx->vjp_ghost, ctx->rhs_out, ctx->stream));
+        wis::GhostArgs ga = ghost_args(ctx, gU_dev, d);
+        ga.sy = sy; ga.sz = sz; ga.sv = sv; ga.off0 = 0;
+        CK(f64 ? wis::ghost_adj_f64(ctx->dim, ga, ctx->vjp_ghost, gU_dev, ctx->stream)
+               : wis::ghost_adj_f32(ctx->dim, ga, ctx->vjp_ghost, gU_dev, ctx->stream));
     }
-    CK(do_pack(ctx, ctx->rhs_out, gU_dev, 0, ctx->stream));
     return WENO_OK;
 }
 

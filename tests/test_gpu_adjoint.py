@@ -139,6 +139,27 @@ def test_autograd_function_matches_vjp():
     s.close()
 
 
+def test_vjp_reads_and_writes_the_callers_arrays():
+    """weno_rhs_vjp works on the caller's interior-only arrays: repeated calls
+    agree bitwise whatever the output held, and an output that is one of the
+    inputs is rejected."""
+    prob, U = P.random_state(3, [13, 11, 9], seed=12, kind="mixed")
+    s = weno.Solver(prob, "fp64")
+    Ud = torch.from_numpy(U).cuda()
+    w = torch.from_numpy(np.random.default_rng(4).normal(size=U.shape)).cuda()
+    a = torch.full_like(Ud, float("nan"))
+    b = torch.full_like(Ud, 3.0)
+    s.rhs_vjp(Ud, w, 0.0, out=a)
+    s.rhs_vjp(Ud, w, 0.0, out=b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and bool(torch.isfinite(a).all())
+    for out in (Ud, w):
+        with pytest.raises(weno.WenoError) as e:
+            weno.weno_rhs_vjp(s.ctx, Ud, w, out, 0.0)
+        assert e.value.status == weno.WENO_ERR_INVALID_ARG
+    s.close()
+
+
 def test_fp32_vjp_close_to_fp64():
     prob, U = P.random_state(3, [16, 12, 10], seed=6, kind="smooth")
     rng = np.random.default_rng(2)
