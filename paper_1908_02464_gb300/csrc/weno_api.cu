@@ -81,10 +81,6 @@ static cudaError_t do_sweep(weno_ctx* c, int dir, const wis::SweepArgs& a, cudaS
     if (c->prec == WENO_FP32) return wis::sweep_f32(c->dim, dir, v, a, s);
     return wis::sweep_mixed(c->dim, dir, v, a, s);
 }
-static cudaError_t do_ghost(weno_ctx* c, const wis::GhostArgs& a, cudaStream_t s)
-{
-    return c->prec == WENO_FP64 ? wis::ghost_f64(c->dim, a, s) : wis::ghost_f32(c->dim, a, s);
-}
 static cudaError_t do_cfl(weno_ctx* c, const wis::CflArgs& a, cudaStream_t s)
 {
     return c->prec == WENO_FP64 ? wis::cfl_f64(c->dim, a, c->nsm, s) : wis::cfl_f32(c->dim, a, c->nsm, s);

@@ -8,7 +8,6 @@ cudaError_t sweep_f32(int dim, int dir, int variant, const SweepArgs& a, cudaStr
 {
     return launch_sweep_t<float, false>(dim, dir, variant, a, s);
 }
-cudaError_t ghost_f32(int dim, const GhostArgs& a, cudaStream_t s) { return launch_ghost_t<float>(dim, a, s); }
 cudaError_t cfl_f32(int dim, const CflArgs& a, int nsm, cudaStream_t s) { return launch_cfl_t<float>(dim, a, nsm, s); }
 cudaError_t totals_f32(int dim, const TotArgs& a, int blocks, cudaStream_t s)
 {

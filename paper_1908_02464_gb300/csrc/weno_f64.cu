@@ -7,7 +7,6 @@ cudaError_t sweep_f64(int dim, int dir, int variant, const SweepArgs& a, cudaStr
 {
     return launch_sweep_t<double, false>(dim, dir, variant, a, s);
 }
-cudaError_t ghost_f64(int dim, const GhostArgs& a, cudaStream_t s) { return launch_ghost_t<double>(dim, a, s); }
 cudaError_t cfl_f64(int dim, const CflArgs& a, int nsm, cudaStream_t s) { return launch_cfl_t<double>(dim, a, nsm, s); }
 cudaError_t totals_f64(int dim, const TotArgs& a, int blocks, cudaStream_t s)
 {

@@ -11,8 +11,6 @@
 //             flux (Sec. 2.4, Eq. eq8-r); the tile then takes the flux
 //             divergence and writes an accumulator, a right-hand side or the
 //             RK3 stage combination (Sec. 4).
-//   k_ghost   three ghost layers of one direction in memory (boundary
-//             conditions), for the adjoint, which reads its halo from memory.
 //   k_cfl     CFL wave-speed max-reduction and admissibility check.
 //   k_dt, k_post   single-thread time-step bookkeeping on the device.
 //   k_totals  conserved totals, FP64 accumulation.
@@ -672,6 +670,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 4 : 2) k_sweep(SweepArgs a)
 }
 
 // ---------------------------------------------------------------- ghosts
+// Boundary conditions of one direction, as the adjoint's ghost-gradient
+// mapping (k_ghost_adj) reads them.
 struct GhostArgs {
     void* U;
     int dir;
@@ -684,75 +684,6 @@ struct GhostArgs {
     DevTime* tm;         // stage time from tm (t + stage_c dt), or t_fixed
     double stage_c, t_fixed;
 };
-
-template <typename T, int DIM>
-__global__ void k_ghost(GhostArgs a)
-{
-    constexpr int NV = DIM + 2;
-    if (a.tm != nullptr && (a.tm->status != 0 || !(a.tm->dt > 0.0))) return;
-    const int d = a.dir;
-    const int nd = a.n[d];
-    // perpendicular extents (i fastest where possible)
-    int e0, e1;   // sizes of the two perpendicular index ranges
-    if (d == 0) { e0 = a.n[1]; e1 = a.n[2]; }
-    else if (d == 1) { e0 = a.n[0]; e1 = a.n[2]; }
-    else { e0 = a.n[0]; e1 = a.n[1]; }
-    const long long P = (long long)e0 * e1;
-    const long long total = 2LL * 3LL * P;
-    const long long sd = d == 0 ? 1LL : (d == 1 ? a.sy : a.sz);
-    T* U = reinterpret_cast<T*>(a.U);
-    double t = a.t_fixed;
-    if (a.tm != nullptr) t = a.tm->t + a.stage_c * a.tm->dt;
-    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-         id += (long long)gridDim.x * blockDim.x) {
-        const long long pp = id % P;
-        const int gl = (int)((id / P) % 3) + 1;
-        const int side = (int)(id / (3 * P));
-        const int p0 = (int)(pp % e0), p1 = (int)(pp / e0);
-        int i, j, k;
-        if (d == 0) { i = 0; j = p0; k = p1; }
-        else if (d == 1) { i = p0; j = 0; k = p1; }
-        else { i = p0; j = p1; k = 0; }
-        // address of the line's cell 0 along d (the along-d index is zero here)
-        const long long base = a.off0 + (long long)i + (long long)j * a.sy + (long long)k * a.sz;
-        const int dst = side == 0 ? -gl : nd - 1 + gl;
-        int bc = side == 0 ? a.bc_lo : a.bc_hi;
-        const double* fixed = nullptr;
-        if (bc == BC_DMR_BOTTOM) {
-            const double x = a.lo0 + (i + 0.5) * a.dx0;
-            if (x < 1.0 / 6.0) { bc = BC_INFLOW; fixed = a.bc_state[0]; }
-            else bc = BC_REFLECT;
-        } else if (bc == BC_DMR_TOP) {
-            const double x = a.lo0 + (i + 0.5) * a.dx0;
-            const double xs = dmr_shock_x(t);
-            fixed = (x < xs) ? a.bc_state[0] : a.bc_state[1];
-            bc = BC_INFLOW;
-        } else if (bc == BC_INFLOW) {
-            fixed = a.bc_state[0];
-        } else if (bc == BC_JET) {
-            const double y = a.lo1 + (j + 0.5) * a.dx1;
-            fixed = (y < JET_HALF_WIDTH) ? a.bc_state[0] : a.bc_state[1];
-            bc = BC_INFLOW;
-        }
-        const long long gdst = base + (long long)dst * sd;
-        if (bc == BC_INFLOW) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) U[gdst + v * a.sv] = T(fixed[v]);
-            continue;
-        }
-        int src;
-        if (bc == BC_TRANSMISSIVE) src = side == 0 ? 0 : nd - 1;
-        else if (bc == BC_REFLECT) src = side == 0 ? gl - 1 : nd - gl;
-        else src = side == 0 ? nd - gl : gl - 1;
-        const long long gsrc = base + (long long)src * sd;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            T val = U[gsrc + v * a.sv];
-            if (bc == BC_REFLECT && v == 1 + d) val = -val;
-            U[gdst + v * a.sv] = val;
-        }
-    }
-}
 
 // ------------------------------------------------------- CFL reduction
 struct CflArgs {

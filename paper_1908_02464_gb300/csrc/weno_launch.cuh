@@ -110,20 +110,6 @@ inline int grid_for(long long work, int threads, int cap)
 }
 
 template <typename T>
-cudaError_t launch_ghost_t(int dim, const GhostArgs& a, cudaStream_t s)
-{
-    long long P;
-    if (a.dir == 0) P = (long long)a.n[1] * a.n[2];
-    else if (a.dir == 1) P = (long long)a.n[0] * a.n[2];
-    else P = (long long)a.n[0] * a.n[1];
-    const int blocks = grid_for(6 * P, 256, 4096);
-    if (dim == 1) k_ghost<T, 1><<<blocks, 256, 0, s>>>(a);
-    else if (dim == 2) k_ghost<T, 2><<<blocks, 256, 0, s>>>(a);
-    else k_ghost<T, 3><<<blocks, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_cfl_t(int dim, const CflArgs& a_in, int nsm, cudaStream_t s)
 {
     // rows x parts units of at least 256 cells each, about 8 blocks per SM
@@ -225,8 +211,6 @@ cudaError_t ghost_adj_f32(int dim, const GhostArgs& a, const void* ghost, void* 
 cudaError_t sweep_f64(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);
 cudaError_t sweep_f32(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);
 cudaError_t sweep_mixed(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);
-cudaError_t ghost_f64(int dim, const GhostArgs& a, cudaStream_t s);
-cudaError_t ghost_f32(int dim, const GhostArgs& a, cudaStream_t s);
 cudaError_t cfl_f64(int dim, const CflArgs& a, int nsm, cudaStream_t s);
 cudaError_t cfl_f32(int dim, const CflArgs& a, int nsm, cudaStream_t s);
 cudaError_t lf_f64(int dim, const CflArgs& a, unsigned long long* out, int nsm, cudaStream_t s);
