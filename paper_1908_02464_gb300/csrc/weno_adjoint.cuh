@@ -19,9 +19,12 @@
 //
 // Accumulation is deterministic: a tile of SEG cells recomputes the SEG + 5
 // faces that touch its cells, writes each face's contribution to its six
-// stencil cells in shared memory (U and F bars for all six, Roe-field bars
-// for the two neighbours, one bar per LLF speed for the cell attaining it),
-// and gathers them per cell in face order.
+// stencil cells in shared memory, and gathers them per cell in face order.
+// A linear-upwind face stores two bar vectors, of the central-flux sum and
+// of the detector difference, and the gather applies their fixed stencil
+// weights; a WENO face stores U and F bars for each of its six cells.  Every
+// face adds Roe-field bars for its two neighbours and one bar per LLF speed
+// for the cell attaining it.
 // Contributions to ghost cells go to a per-line buffer that a second kernel
 // maps back through the boundary conditions.
 #pragma once
@@ -306,9 +309,11 @@ struct VjpSmem {
     static constexpr int LNF = LINES * NF, LNC = LINES * NC;
     static constexpr int NQ = CellLayout<DIM>::NQ;
     static constexpr int NV = DIM + 2;
-    // per face: U and F bars of the six stencil cells, Roe-field bars of
-    // cells 2 and 3 (the face's neighbours), the three LLF speed bars, and
-    // (as one int) the stencil slots of the cells attaining the speeds
+    // per face: U and F bars of the six stencil cells (a linear-upwind face
+    // uses the first 2 NV entries only, see k_vjp), Roe-field bars of cells
+    // 2 and 3 (the face's neighbours), the three LLF speed bars, and (as one
+    // int) the stencil slots of the cells attaining the speeds and the kind
+    // of face
     static constexpr int NUF = 2 * NV;
     static constexpr int NRB = DIM + 2;
     static constexpr int NFB = 6 * NUF + 2 * NRB + 3;
@@ -342,10 +347,11 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ][NC][LINES] cell records
     T* wq = cq + NQ * LNC;                    // [NV][NC][LINES] cotangent
-    T* UF = wq + NV * LNC;                    // [NF][LINES][6][NUF] U and F bars of the stencil cells
+    T* UF = wq + NV * LNC;                    // [NF][LINES][6][NUF] U and F bars (see below)
     T* RB = UF + LNF * 6 * NUF;               // [NF][LINES][2][NRB] Roe-field bars of cells 2 and 3
     T* SP = RB + LNF * 2 * NRB;               // [NF][LINES][3] LLF speed bars
-    int* SL = reinterpret_cast<int*>(SP + LNF * 3);   // [NF][LINES] slots attaining the speeds
+    int* SL = reinterpret_cast<int*>(SP + LNF * 3);   // [NF][LINES] slots attaining the speeds, face kind
+    constexpr int WENO_FACE = 1 << 12;
 
     const int nd = a.n[DIR];
     const int c0 = blockIdx.x * SEG;
@@ -386,7 +392,6 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
             for (int v = 0; v < NV; ++v) wq[v * LNC + idx] = T(0);
         }
     }
-    for (int idx = threadIdx.x; idx < LNF * NFB; idx += NT) UF[idx] = T(0);
     __syncthreads();
 
     // ---- per face: forward recompute and reverse -------------------------
@@ -399,7 +404,10 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
         if (l >= nlx || face < 0 || face > nd) continue;
         // stencil cell j-2 = face-3 sits at position f of line l
         auto rec = [&](int m, int kk) -> T { return cq[kk * LNC + (f + m) * LINES + l]; };
-        T* UFf = UF + (size_t)ff * 6 * NUF;    // U and F bars of the six stencil cells
+        // a WENO face: U and F bars of each of the six stencil cells; a
+        // linear-upwind face: the bars of its detector difference (U slots)
+        // and of its central-flux sum (F slots) in the first NUF entries
+        T* UFf = UF + (size_t)ff * 6 * NUF;
         T* RBf = RB + (size_t)ff * 2 * NRB;    // Roe-field bars of cells 2 and 3
         // cotangent of the face flux: (w_{right} - w_{left}) / dx
         T phi[NV];
@@ -438,15 +446,14 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
 #pragma unroll
         for (int s = 0; s < NV; ++s) wb[s] = T(0);
         if (smooth) {
-            // F = [central(F) + R (alpha o w)] / 60
+            // F = [central(F) + R (alpha o w)] / 60; the gather applies the
+            // central weights to the bar Fb of the sum
             T Fb[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Fb[v] = phi[v] * T(1.0 / 60.0);
-            const T cf[6] = {T(1), T(-8), T(37), T(37), T(-8), T(1)};
-#pragma unroll
-            for (int m = 0; m < 6; ++m)
-#pragma unroll
-                for (int v = 0; v < NV; ++v) UFf[m * NUF + CL::F + v] += cf[m] * Fb[v];
+            for (int v = 0; v < NV; ++v) {
+                Fb[v] = phi[v] * T(1.0 / 60.0);
+                UFf[CL::F + v] = Fb[v];
+            }
             T aw[NV], awb[NV];
             aw[0] = am * w[0];
 #pragma unroll
@@ -538,8 +545,8 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
                 proj_all_adj<T, DIM, DIR>(r, xf, gbar[m], xfb, rb);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    UFf[m * NUF + CL::U + v] += xub[v];
-                    UFf[m * NUF + CL::F + v] += xfb[v];
+                    UFf[m * NUF + CL::U + v] = xub[v];
+                    UFf[m * NUF + CL::F + v] = xfb[v];
                 }
             }
         }
@@ -548,15 +555,22 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
 #pragma unroll
         for (int v = 0; v < NV; ++v) dUb[v] = T(0);
         proj_all_adj<T, DIM, DIR>(r, dU, wb, dUb, rb);
-        const T cd[6] = {T(1), T(-5), T(10), T(-10), T(5), T(-1)};
+        if (smooth) {
 #pragma unroll
-        for (int m = 0; m < 6; ++m)
+            for (int v = 0; v < NV; ++v) UFf[CL::U + v] = dUb[v];
+        } else {
+            const T cd[6] = {T(1), T(-5), T(10), T(-10), T(5), T(-1)};
 #pragma unroll
-            for (int v = 0; v < NV; ++v) UFf[m * NUF + CL::U + v] += cd[m] * dUb[v];
-        SP[ff * 3 + 0] += alb_m;
-        SP[ff * 3 + 1] += alb_0;
-        SP[ff * 3 + 2] += alb_p;
-        SL[ff] = im | (i0 << 4) | (ip << 8);
+            for (int m = 0; m < 6; ++m)
+#pragma unroll
+                for (int v = 0; v < NV; ++v) UFf[m * NUF + CL::U + v] += cd[m] * dUb[v];
+        }
+        SP[ff * 3 + 0] = alb_m;
+        SP[ff * 3 + 1] = alb_0;
+        SP[ff * 3 + 2] = alb_p;
+        SL[ff] = im | (i0 << 4) | (ip << 8) | (smooth ? 0 : WENO_FACE);
+#pragma unroll
+        for (int kk = 0; kk < 2 * NRB; ++kk) RBf[kk] = T(0);
         roe_adj<T, DIM>(ga, gb, gamma, r, rb, RBf, RBf + NRB);
     }
     __syncthreads();
@@ -575,23 +589,36 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
         T qb[NQ];
 #pragma unroll
         for (int kk = 0; kk < NQ; ++kk) qb[kk] = T(0);
-        for (int fi = cell - 2; fi <= cell + 3; ++fi) {
+        // central-flux and detector weights of stencil slot m
+        constexpr T cf[6] = {T(1), T(-8), T(37), T(37), T(-8), T(1)};
+        constexpr T cd[6] = {T(1), T(-5), T(10), T(-10), T(5), T(-1)};
+#pragma unroll
+        for (int m = 5; m >= 0; --m) {
+            const int fi = cell - m + 3;   // faces in increasing order
             if (fi < 0 || fi > nd) continue;
             const int f = fi - (c0 - 2);
             if (f < 0 || f >= NF) continue;
             const int ff = f * LINES + l;
-            const int m = cell - fi + 3;
+            const int sl = SL[ff];
             // the entries this cell receives from face fi, in the record
             // layout; the others are zero for it
-            const T* uf = UF + ((size_t)ff * 6 + m) * NUF;
+            if (sl & WENO_FACE) {
+                const T* uf = UF + ((size_t)ff * 6 + m) * NUF;
 #pragma unroll
-            for (int kk = 0; kk < NUF; ++kk) qb[kk] += uf[kk];
+                for (int kk = 0; kk < NUF; ++kk) qb[kk] += uf[kk];
+            } else {
+                const T* uf = UF + (size_t)ff * 6 * NUF;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    qb[CL::U + v] = fmaT(cd[m], uf[CL::U + v], qb[CL::U + v]);
+                    qb[CL::F + v] = fmaT(cf[m], uf[CL::F + v], qb[CL::F + v]);
+                }
+            }
             if (m == 2 || m == 3) {
                 const T* rbp = RB + ((size_t)ff * 2 + (m - 2)) * NRB;
 #pragma unroll
                 for (int kk = 0; kk < NRB; ++kk) qb[CL::SU + kk] += rbp[kk];
             }
-            const int sl = SL[ff];
             if ((sl & 15) == m) qb[CL::LM] += SP[ff * 3 + 0];
             if (((sl >> 4) & 15) == m) qb[CL::L0] += SP[ff * 3 + 1];
             if (((sl >> 8) & 15) == m) qb[CL::LP] += SP[ff * 3 + 2];
