@@ -25,6 +25,14 @@
 // weights; a WENO face stores U and F bars for each of its six cells.  Every
 // face adds Roe-field bars for its two neighbours and one bar per LLF speed
 // for the cell attaining it.
+//
+// Each direction runs in two passes over the same tiles.  Pass 0 takes the
+// linear-upwind faces, writes (or adds) the gradient, and flags each tile
+// that has a WENO face among the faces it recomputes.  Pass 1 runs on the
+// flagged tiles only, takes their WENO faces and adds their contributions.
+// The WENO reverse needs the registers of the 6 x nvar projections and
+// their bars; keeping it out of pass 0 lets the common linear-upwind tiles
+// run with far fewer registers and more resident warps.
 // Contributions to ghost cells go to a per-line buffer that a second kernel
 // maps back through the boundary conditions.
 #pragma once
@@ -50,7 +58,9 @@ __device__ __forceinline__ void cell_adj(const T* U, T gamma, const T* qb, T* Ub
     for (int k = 0; k < DIM; ++k) m2 = fmaT(U[1 + k], U[1 + k], m2);
     const T E = U[DIM + 1];
     const T p = gm1 * fmaT(T(-0.5) * irho, m2, E);
-    const T c = Ar<T>::sqrt_(gamma * p * irho);
+    const T c2 = gamma * p * irho;
+    const T ic = Ar<T>::rsqrt_(c2);   // 1/c; c as in the forward record
+    const T c = c2 * ic;
     const T un = U[1 + DIR] * irho;
     const T Ep = E + p;
 
@@ -73,7 +83,7 @@ __device__ __forceinline__ void cell_adj(const T* U, T gamma, const T* qb, T* Ub
     Ub[DIM + 1] += Epb; pb += Epb;
     Ub[1 + DIR] += unb * irho; irhob += unb * U[1 + DIR];
     // c = sqrt(gamma p irho)
-    const T cc = cb / (T(2) * c);
+    const T cc = cb * T(0.5) * ic;
     pb += cc * gamma * irho; irhob += cc * gamma * p;
     // p = gm1 (E - irho m2 / 2)
     Ub[DIM + 1] += pb * gm1; irhob -= pb * gm1 * T(0.5) * m2; m2b -= pb * gm1 * T(0.5) * irho;
@@ -175,7 +185,7 @@ __device__ __forceinline__ void roe_adj(GA get_a, GB get_b, T gamma, const Roe<T
     using CL = CellLayout<DIM>;
     const T gm1 = gamma - T(1);
     const T sa = get_a(CL::SQ), sb = get_b(CL::SQ);
-    const T inv = Ar<T>::rcp(sa + sb);
+    const T inv = Ar<T>::rcp_f(sa + sb);   // as in roe_state
     // b1 = gm1 ic^2; c = c2 ic (= sqrt c2); ic = c2^-1/2; c2 = gm1 (H - hq2)
     rb.ic += rb.b1 * gm1 * T(2) * r.ic;
     const T ic3 = r.ic * r.ic * r.ic;
@@ -277,7 +287,10 @@ struct VjpArgs {
     const void* W;      // cotangent, interior only
     void* G;            // gradient, interior only (written / accumulated)
     void* ghost;        // [line][6][NV] gradients of ghost cells
-    int accumulate;     // 0: G = ..., 1: G += ...
+    int* n_weno_tiles;  // tiles of this direction with a WENO face (zero before pass 0)
+    int* weno_tiles;    // their linear tile indices, in no particular order (pass 0 appends)
+    int tiles[3];       // tile grid of this direction (set by the launcher)
+    int accumulate;     // 0: G = ..., 1: G += ... (pass 0; pass 1 always adds)
     int n[3];
     long long sy, sz, sv, off0;
     double inv_dx, eps_h, gamma, eps, c_lambda;
@@ -300,7 +313,7 @@ template <typename T, int DIM, int DIR> struct VjpTile {
     static constexpr int NT = LINES * (SEG + 5);
 };
 
-template <typename T, int DIM, int DIR>
+template <typename T, int DIM, int DIR, int PASS>
 struct VjpSmem {
     static constexpr int LINES = VjpTile<T, DIM, DIR>::LINES;
     static constexpr int SEG = VjpTile<T, DIM, DIR>::SEG;
@@ -309,58 +322,56 @@ struct VjpSmem {
     static constexpr int LNF = LINES * NF, LNC = LINES * NC;
     static constexpr int NQ = CellLayout<DIM>::NQ;
     static constexpr int NV = DIM + 2;
-    // per face: U and F bars of the six stencil cells (a linear-upwind face
-    // uses the first 2 NV entries only, see k_vjp), Roe-field bars of cells
-    // 2 and 3 (the face's neighbours), the three LLF speed bars, and (as one
-    // int) the stencil slots of the cells attaining the speeds and the kind
-    // of face
+    // per face: U and F bars of the six stencil cells (pass 1) or the two
+    // bar vectors of a linear-upwind face (pass 0, NUF entries), Roe-field
+    // bars of cells 2 and 3 (the face's neighbours), the three LLF speed
+    // bars, and (as one int) the stencil slots of the cells attaining the
+    // speeds and whether the pass takes the face
     static constexpr int NUF = 2 * NV;
+    static constexpr int NUFF = PASS == 0 ? NUF : 6 * NUF;
     static constexpr int NRB = DIM + 2;
-    static constexpr int NFB = 6 * NUF + 2 * NRB + 3;
+    static constexpr int NFB = NUFF + 2 * NRB + 3;
     static constexpr size_t bytes =
         sizeof(T) * ((size_t)NQ * LNC + (size_t)NV * LNC + (size_t)LNF * NFB) + sizeof(int) * (size_t)LNF;
 };
 
-// Residency of the adjoint kernel: the per-face reverse pass needs more than
-// 255 registers, which leaves 8 warps per SM.  FP64 is held to 4 CTAs per SM
-// by shared memory anyway and keeps its FP64 pipe 79-85% busy; FP32 code
-// needs more warps to hide its latencies, so its register count is capped at
-// 128 (8 CTAs of the 64-thread x tiles, 2 of the 256-thread y/z tiles, which
-// their shared memory allows) at the cost of spills: the 256^3 FP32 VJP went
-// from 10.0 to 7.2 ms (same-GPU A/B, same result).
-template <typename T, int NT> struct VjpMinBlocks {
-    static constexpr int value = sizeof(T) == 4 ? (NT == 64 ? 8 : 2) : 1;
+// Residency of the WENO pass: its per-face reverse needs more than 255
+// registers, which leaves 8 warps per SM in FP64.  FP32 code needs more
+// warps to hide its latencies, so its register count is capped at 128 (8
+// CTAs of the 64-thread x tiles, 2 of the 256-thread y/z tiles) at the cost
+// of spills.
+template <typename T, int NT, int PASS> struct VjpMinBlocks {
+    static constexpr int value = PASS == 0 ? 1 : (sizeof(T) == 4 ? (NT == 64 ? 8 : 2) : 1);
 };
 
-// one direction of the VJP: tile = LINES grid lines x SEG cells; shared
-// arrays hold position p of line l at p * LINES + l
-template <typename T, int DIM, int DIR>
-__global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpTile<T, DIM, DIR>::NT>::value)
-    k_vjp(VjpArgs a)
+// One tile of one direction of the VJP: tile (bx, by, bz) = LINES grid lines
+// x SEG cells; shared arrays hold position p of line l at p * LINES + l.
+// Returns (to every thread, pass 0) whether a face of the tile took WENO.
+template <typename T, int DIM, int DIR, int PASS>
+__device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int bz, unsigned char* smem_raw)
 {
     using CL = CellLayout<DIM>;
-    using SM = VjpSmem<T, DIM, DIR>;
+    using SM = VjpSmem<T, DIM, DIR, PASS>;
     constexpr int NV = DIM + 2, NQ = CL::NQ, SEG = SM::SEG, NF = SM::NF;
     constexpr int LINES = SM::LINES, LNF = SM::LNF, LNC = SM::LNC;
     constexpr int NT = VjpTile<T, DIM, DIR>::NT;
-    constexpr int NUF = SM::NUF, NRB = SM::NRB, NFB = SM::NFB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NUF = SM::NUF, NUFF = SM::NUFF, NRB = SM::NRB;
     T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ][NC][LINES] cell records
     T* wq = cq + NQ * LNC;                    // [NV][NC][LINES] cotangent
-    T* UF = wq + NV * LNC;                    // [NF][LINES][6][NUF] U and F bars (see below)
-    T* RB = UF + LNF * 6 * NUF;               // [NF][LINES][2][NRB] Roe-field bars of cells 2 and 3
+    T* UF = wq + NV * LNC;                    // [NF][LINES][NUFF] U and F bars (see below)
+    T* RB = UF + LNF * NUFF;                  // [NF][LINES][2][NRB] Roe-field bars of cells 2 and 3
     T* SP = RB + LNF * 2 * NRB;               // [NF][LINES][3] LLF speed bars
-    int* SL = reinterpret_cast<int*>(SP + LNF * 3);   // [NF][LINES] slots attaining the speeds, face kind
-    constexpr int WENO_FACE = 1 << 12;
+    int* SL = reinterpret_cast<int*>(SP + LNF * 3);   // [NF][LINES] slots attaining the speeds, face taken
+    constexpr int SKIP = 1 << 12;   // the face belongs to the other pass
 
     const int nd = a.n[DIR];
-    const int c0 = blockIdx.x * SEG;
+    const int c0 = bx * SEG;
     // line coordinates: the two indices other than DIR; the lines of a
     // multi-line tile are consecutive in x
     int ix0 = 0, j = 0, k = 0;
-    if (DIR == 0) { j = blockIdx.y; k = blockIdx.z; }
-    else if (DIR == 1) { ix0 = blockIdx.y * LINES; k = blockIdx.z; }
-    else { ix0 = blockIdx.y * LINES; j = blockIdx.z; }
+    if (DIR == 0) { j = by; k = bz; }
+    else if (DIR == 1) { ix0 = by * LINES; k = bz; }
+    else { ix0 = by * LINES; j = bz; }
     const int nlx = DIR == 0 ? 1 : (a.n[0] - ix0 < LINES ? a.n[0] - ix0 : LINES);   // lines present
     const long long sd = DIR == 0 ? 1LL : (DIR == 1 ? a.sy : a.sz);
     const long long base0 = a.off0 + (long long)ix0 + (long long)j * a.sy + (long long)k * a.sz;
@@ -398,16 +409,17 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
     const T slim = T(a.slim);
     const T lam_k = T(a.c_lambda / 3600.0);
     const T eps = T(a.eps), inv_dx = T(a.inv_dx);
+    bool has_weno = false;
     for (int ff = threadIdx.x; ff < LNF; ff += NT) {
         const int f = ff / LINES, l = ff - (ff / LINES) * LINES;
         const int face = c0 - 2 + f;            // face i' between cells i'-1 and i'
         if (l >= nlx || face < 0 || face > nd) continue;
         // stencil cell j-2 = face-3 sits at position f of line l
         auto rec = [&](int m, int kk) -> T { return cq[kk * LNC + (f + m) * LINES + l]; };
-        // a WENO face: U and F bars of each of the six stencil cells; a
-        // linear-upwind face: the bars of its detector difference (U slots)
-        // and of its central-flux sum (F slots) in the first NUF entries
-        T* UFf = UF + (size_t)ff * 6 * NUF;
+        // pass 1 (WENO faces): U and F bars of each of the six stencil
+        // cells; pass 0 (linear-upwind faces): the bars of the detector
+        // difference (U slots) and of the central-flux sum (F slots)
+        T* UFf = UF + (size_t)ff * NUFF;
         T* RBf = RB + (size_t)ff * 2 * NRB;    // Roe-field bars of cells 2 and 3
         // cotangent of the face flux: (w_{right} - w_{left}) / dx
         T phi[NV];
@@ -432,6 +444,11 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
         bool smooth = a.hybrid != 0;
 #pragma unroll
         for (int s = 0; s < NV; ++s) smooth = smooth && abs_lt(w[s], lim);
+        if (smooth != (PASS == 0)) {   // the other pass takes this face
+            has_weno = has_weno || !smooth;
+            SL[ff] = SKIP;
+            continue;
+        }
         // LLF speeds and the cells attaining them
         T am = rec(0, CL::LM), a0 = rec(0, CL::L0), ap = rec(0, CL::LP);
         int im = 0, i0 = 0, ip = 0;
@@ -445,7 +462,7 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
         T wb[NV];
 #pragma unroll
         for (int s = 0; s < NV; ++s) wb[s] = T(0);
-        if (smooth) {
+        if constexpr (PASS == 0) {
             // F = [central(F) + R (alpha o w)] / 60; the gather applies the
             // central weights to the bar Fb of the sum
             T Fb[NV];
@@ -555,7 +572,7 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
 #pragma unroll
         for (int v = 0; v < NV; ++v) dUb[v] = T(0);
         proj_all_adj<T, DIM, DIR>(r, dU, wb, dUb, rb);
-        if (smooth) {
+        if constexpr (PASS == 0) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) UFf[CL::U + v] = dUb[v];
         } else {
@@ -568,12 +585,12 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
         SP[ff * 3 + 0] = alb_m;
         SP[ff * 3 + 1] = alb_0;
         SP[ff * 3 + 2] = alb_p;
-        SL[ff] = im | (i0 << 4) | (ip << 8) | (smooth ? 0 : WENO_FACE);
+        SL[ff] = im | (i0 << 4) | (ip << 8);
 #pragma unroll
         for (int kk = 0; kk < 2 * NRB; ++kk) RBf[kk] = T(0);
         roe_adj<T, DIM>(ga, gb, gamma, r, rb, RBf, RBf + NRB);
     }
-    __syncthreads();
+    const bool any_weno = __syncthreads_or(has_weno ? 1 : 0) != 0;
 
     // ---- gather per cell: faces i' in [i-2, i+3], stencil slot m = i - i' + 3
     T* Gg = reinterpret_cast<T*>(a.G);
@@ -589,6 +606,7 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
         T qb[NQ];
 #pragma unroll
         for (int kk = 0; kk < NQ; ++kk) qb[kk] = T(0);
+        bool touched = false;
         // central-flux and detector weights of stencil slot m
         constexpr T cf[6] = {T(1), T(-8), T(37), T(37), T(-8), T(1)};
         constexpr T cd[6] = {T(1), T(-5), T(10), T(-10), T(5), T(-1)};
@@ -600,14 +618,16 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
             if (f < 0 || f >= NF) continue;
             const int ff = f * LINES + l;
             const int sl = SL[ff];
+            if (sl & SKIP) continue;
+            touched = true;
             // the entries this cell receives from face fi, in the record
             // layout; the others are zero for it
-            if (sl & WENO_FACE) {
-                const T* uf = UF + ((size_t)ff * 6 + m) * NUF;
+            if constexpr (PASS == 1) {
+                const T* uf = UF + (size_t)ff * NUFF + m * NUF;
 #pragma unroll
                 for (int kk = 0; kk < NUF; ++kk) qb[kk] += uf[kk];
             } else {
-                const T* uf = UF + (size_t)ff * 6 * NUF;
+                const T* uf = UF + (size_t)ff * NUFF;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     qb[CL::U + v] = fmaT(cd[m], uf[CL::U + v], qb[CL::U + v]);
@@ -623,6 +643,7 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
             if (((sl >> 4) & 15) == m) qb[CL::L0] += SP[ff * 3 + 1];
             if (((sl >> 8) & 15) == m) qb[CL::LP] += SP[ff * 3 + 2];
         }
+        if (PASS == 1 && !touched) continue;
         const int pc = cell - (c0 - 5);
         T U[NV], Ub[NV];
 #pragma unroll
@@ -632,7 +653,7 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
             const long long g = base0 + l + (long long)cell * sd;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                if (a.accumulate) Gg[g + v * a.sv] += Ub[v];
+                if (PASS == 1 || a.accumulate) Gg[g + v * a.sv] += Ub[v];
                 else Gg[g + v * a.sv] = Ub[v];
             }
         } else {
@@ -641,7 +662,35 @@ __global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpT
                                             : (DIR == 1 ? ((long long)k * a.n[0] + i) : ((long long)j * a.n[0] + i));
             const int slot = gl ? (-cell - 1) : (3 + cell - nd);   // 0..2 left (-1,-2,-3), 3..5 right
 #pragma unroll
-            for (int v = 0; v < NV; ++v) ghost[(line * 6 + slot) * NV + v] = Ub[v];
+            for (int v = 0; v < NV; ++v) {
+                if (PASS == 1) ghost[(line * 6 + slot) * NV + v] += Ub[v];
+                else ghost[(line * 6 + slot) * NV + v] = Ub[v];
+            }
+        }
+    }
+    return any_weno;
+}
+
+// Pass 0: one CTA per tile; a tile with a WENO face appends its index to
+// the list.  Pass 1: a grid of resident CTAs takes the listed tiles in turn
+// (each tile writes only its own cells and ghost slots, so the order in
+// which the tiles are taken does not change the result).
+template <typename T, int DIM, int DIR, int PASS>
+__global__ void __launch_bounds__(VjpTile<T, DIM, DIR>::NT, VjpMinBlocks<T, VjpTile<T, DIM, DIR>::NT, PASS>::value)
+    k_vjp(VjpArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (PASS == 0) {
+        const bool any = vjp_tile<T, DIM, DIR, 0>(a, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+        if (any && threadIdx.x == 0)
+            a.weno_tiles[atomicAdd(a.n_weno_tiles, 1)] = blockIdx.x + a.tiles[0] * (blockIdx.y + a.tiles[1] * blockIdx.z);
+    } else {
+        const int n = *a.n_weno_tiles;
+        for (int it = blockIdx.x; it < n; it += gridDim.x) {
+            const int t = a.weno_tiles[it];
+            const int bx = t % a.tiles[0], byz = t / a.tiles[0];
+            vjp_tile<T, DIM, DIR, 1>(a, bx, byz % a.tiles[1], byz / a.tiles[1], smem_raw);
+            __syncthreads();   // shared memory is reused by the next tile
         }
     }
 }

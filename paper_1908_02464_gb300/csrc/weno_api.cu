@@ -15,6 +15,7 @@
 // step is not counted and the state stays in cur.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -45,6 +46,8 @@ struct weno_ctx {
     void* stage_io = nullptr;   // interior-size staging for host copies
     void* vjp_w = nullptr;      // ghosted cotangent (ghost layers stay zero)
     void* vjp_ghost = nullptr;  // per-line ghost-cell gradients
+    int* vjp_tiles = nullptr;   // per direction: count (entries 0..2), then lists of tiles with WENO faces
+    long long vjp_tiles_max = 0;
     unsigned long long* alpha_g = nullptr;   // global LF speeds [stage 0..3][dir][3]
     DevTime* tm = nullptr;
     DevTime* tm_host = nullptr; // pinned
@@ -291,6 +294,7 @@ static void free_all(weno_ctx* c)
     if (c->stage_io) cudaFree(c->stage_io);
     if (c->vjp_w) cudaFree(c->vjp_w);
     if (c->vjp_ghost) cudaFree(c->vjp_ghost);
+    if (c->vjp_tiles) cudaFree(c->vjp_tiles);
     if (c->alpha_g) cudaFree(c->alpha_g);
     if (c->tm) cudaFree(c->tm);
     if (c->tm_host) cudaFreeHost(c->tm_host);
@@ -612,6 +616,21 @@ weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, vo
         }
         CK(cudaMalloc(&ctx->vjp_ghost, (size_t)lines * 6 * ctx->nv * ctx->esz));
     }
+    if (!ctx->vjp_tiles) {
+        long long tiles = 0;
+        for (int d = 0; d < ctx->dim; ++d) {
+            const long long t = ctx->prec == WENO_FP64 ? wis::vjp_tiles_f64(ctx->dim, d, ctx->n)
+                                                       : wis::vjp_tiles_f32(ctx->dim, d, ctx->n);
+            if (t > tiles) tiles = t;
+        }
+        if (tiles > INT_MAX) {
+            ctx->err = "grid too large for the adjoint's tile lists";
+            return WENO_ERR_INVALID_ARG;
+        }
+        CK(cudaMalloc(&ctx->vjp_tiles, (size_t)(4 + 3 * tiles) * sizeof(int)));
+        ctx->vjp_tiles_max = tiles;
+    }
+    CK(cudaMemsetAsync(ctx->vjp_tiles, 0, 3 * sizeof(int), ctx->stream));
     // the caller's interior-only arrays with plain strides: the tiles compute
     // the ghost cells of U from the boundary conditions while staging
     long long sy, sz, sv;
@@ -624,6 +643,8 @@ weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, vo
         a.W = w_dev;
         a.G = gU_dev;
         a.ghost = ctx->vjp_ghost;
+        a.n_weno_tiles = ctx->vjp_tiles + d;
+        a.weno_tiles = ctx->vjp_tiles + 4 + d * ctx->vjp_tiles_max;
         a.accumulate = d > 0;
         for (int k = 0; k < 3; ++k) a.n[k] = ctx->n[k];
         a.sy = sy; a.sz = sz; a.sv = sv; a.off0 = 0;

@@ -23,6 +23,7 @@ cudaError_t vjp_f32(int dim, int dir, const VjpArgs& a, cudaStream_t s)
 {
     return launch_vjp_t<float>(dim, dir, a, s);
 }
+long long vjp_tiles_f32(int dim, int dir, const int* n) { return vjp_tiles_t<float>(dim, dir, n); }
 cudaError_t ghost_adj_f32(int dim, const GhostArgs& a, const void* ghost, void* G, cudaStream_t s)
 {
     return launch_ghost_adj_t<float>(dim, a, ghost, G, s);

@@ -22,6 +22,7 @@ cudaError_t vjp_f64(int dim, int dir, const VjpArgs& a, cudaStream_t s)
 {
     return launch_vjp_t<double>(dim, dir, a, s);
 }
+long long vjp_tiles_f64(int dim, int dir, const int* n) { return vjp_tiles_t<double>(dim, dir, n); }
 cudaError_t ghost_adj_f64(int dim, const GhostArgs& a, const void* ghost, void* G, cudaStream_t s)
 {
     return launch_ghost_adj_t<double>(dim, a, ghost, G, s);

@@ -158,25 +158,58 @@ cudaError_t launch_pack_t(const void* src, void* dst, int nv, const int* n, long
     return cudaGetLastError();
 }
 
+// grid of the adjoint tiles of one direction (both passes use it)
+template <typename T, int DIM, int DIR>
+dim3 vjp_grid(const int* n)
+{
+    using TL = VjpTile<T, DIM, DIR>;
+    int e0, e1;
+    // y and z tiles hold TL::LINES lines consecutive in x
+    if (DIR == 0) { e0 = n[1]; e1 = n[2]; }
+    else if (DIR == 1) { e0 = (n[0] + TL::LINES - 1) / TL::LINES; e1 = n[2]; }
+    else { e0 = (n[0] + TL::LINES - 1) / TL::LINES; e1 = n[1]; }
+    return dim3((n[DIR] + TL::SEG - 1) / TL::SEG, e0, e1);
+}
+
+template <typename T, int DIM, int DIR, int PASS>
+cudaError_t launch_vjp_pass(const VjpArgs& a, cudaStream_t s)
+{
+    using SM = VjpSmem<T, DIM, DIR, PASS>;
+    constexpr int NT = VjpTile<T, DIM, DIR>::NT;
+    auto kern = k_vjp<T, DIM, DIR, PASS>;
+    static int resident = 0;   // CTAs per SM (pass 1 grid)
+    if (resident == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, NT, SM::bytes);
+        if (e != cudaSuccess) return e;
+        if (resident < 1) resident = 1;
+    }
+    const dim3 g = vjp_grid<T, DIM, DIR>(a.n);
+    VjpArgs b = a;
+    b.tiles[0] = (int)g.x; b.tiles[1] = (int)g.y; b.tiles[2] = (int)g.z;
+    if (PASS == 0) {
+        kern<<<g, NT, SM::bytes, s>>>(b);
+    } else {
+        int dev = 0, nsm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const long long tiles = (long long)g.x * g.y * g.z;
+        const long long blocks = (long long)resident * nsm < tiles ? (long long)resident * nsm : tiles;
+        kern<<<(unsigned)(blocks > 0 ? blocks : 1), NT, SM::bytes, s>>>(b);
+    }
+    return cudaGetLastError();
+}
+
+// pass 0 (linear-upwind faces, lists the tiles with WENO faces), then pass 1
+// (the WENO faces of the listed tiles)
 template <typename T, int DIM, int DIR>
 cudaError_t launch_vjp_one(const VjpArgs& a, cudaStream_t s)
 {
-    using SM = VjpSmem<T, DIM, DIR>;
-    auto kern = k_vjp<T, DIM, DIR>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::bytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    int e0, e1;
-    // y and z tiles hold SM::LINES lines consecutive in x
-    if (DIR == 0) { e0 = a.n[1]; e1 = a.n[2]; }
-    else if (DIR == 1) { e0 = (a.n[0] + SM::LINES - 1) / SM::LINES; e1 = a.n[2]; }
-    else { e0 = (a.n[0] + SM::LINES - 1) / SM::LINES; e1 = a.n[1]; }
-    dim3 grid((a.n[DIR] + SM::SEG - 1) / SM::SEG, e0, e1);
-    kern<<<grid, VjpTile<T, DIM, DIR>::NT, SM::bytes, s>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = launch_vjp_pass<T, DIM, DIR, 0>(a, s);
+    if (e != cudaSuccess) return e;
+    return launch_vjp_pass<T, DIM, DIR, 1>(a, s);
 }
 
 template <typename T>
@@ -187,6 +220,17 @@ cudaError_t launch_vjp_t(int dim, int dir, const VjpArgs& a, cudaStream_t s)
     if (dir == 0) return launch_vjp_one<T, 3, 0>(a, s);
     if (dir == 1) return launch_vjp_one<T, 3, 1>(a, s);
     return launch_vjp_one<T, 3, 2>(a, s);
+}
+
+// number of adjoint tiles of one direction (the most VjpArgs::weno_tiles holds)
+template <typename T>
+long long vjp_tiles_t(int dim, int dir, const int* n)
+{
+    dim3 g;
+    if (dim == 1) g = vjp_grid<T, 1, 0>(n);
+    else if (dim == 2) g = dir == 0 ? vjp_grid<T, 2, 0>(n) : vjp_grid<T, 2, 1>(n);
+    else g = dir == 0 ? vjp_grid<T, 3, 0>(n) : (dir == 1 ? vjp_grid<T, 3, 1>(n) : vjp_grid<T, 3, 2>(n));
+    return (long long)g.x * g.y * g.z;
 }
 
 template <typename T>
@@ -206,6 +250,8 @@ cudaError_t launch_ghost_adj_t(int dim, const GhostArgs& a, const void* ghost, v
 // per-precision entry points (one translation unit each)
 cudaError_t vjp_f64(int dim, int dir, const VjpArgs& a, cudaStream_t s);
 cudaError_t vjp_f32(int dim, int dir, const VjpArgs& a, cudaStream_t s);
+long long vjp_tiles_f64(int dim, int dir, const int* n);
+long long vjp_tiles_f32(int dim, int dir, const int* n);
 cudaError_t ghost_adj_f64(int dim, const GhostArgs& a, const void* ghost, void* G, cudaStream_t s);
 cudaError_t ghost_adj_f32(int dim, const GhostArgs& a, const void* ghost, void* G, cudaStream_t s);
 cudaError_t sweep_f64(int dim, int dir, int variant, const SweepArgs& a, cudaStream_t s);

@@ -168,3 +168,97 @@ def test_fp32_vjp_close_to_fp64():
     g32 = _vjp(prob, U, w, "fp32")
     rel = np.max(np.abs(g32 - g64)) / np.max(np.abs(g64))
     assert rel < 1e-3, rel
+
+
+def _weno_face_fraction(prob, U):
+    s = weno.Solver(prob, "fp64")
+    f = s.face_flags(torch.from_numpy(U).cuda()).cpu().numpy()
+    s.close()
+    return 1.0 - float(np.mean(f))
+
+
+def test_vjp_entries_across_tiles():
+    """A 150 x 130 grid: several adjoint tiles per line (59 cells each in
+    FP64), with WENO faces in some tiles and none in others, so that the
+    linear-upwind pass and the WENO pass (flagged tiles only) both write the
+    gradient.  (J^T w)_k = <w, J e_k> from the oracle's JVP, at cells on both
+    sides of every tile edge along x and y, and at random cells.  Bar: 1e-10
+    relative, or ten times the oracle's own change of the entry under
+    one-ulp input perturbations (the WENO weights' derivatives are
+    ill-conditioned where lambda beta ~ eps), capped at 1e-7."""
+    prob, U = P.random_state(2, [150, 130], seed=21, kind="mixed")
+    frac = _weno_face_fraction(prob, U)
+    assert 0.01 < frac < 0.5, frac
+    rng = np.random.default_rng(8)
+    prng = np.random.default_rng(99)
+    w = rng.normal(size=U.shape)
+    g = _vjp(prob, U, w)
+    edge = [0, 1, 2, 56, 57, 58, 59, 60, 61, 62, 115, 116, 117, 118, 119, 120, 121, 127, 128, 129]
+    cells = [(int(rng.integers(0, 130)), i) for i in edge + [147, 148, 149]]
+    cells += [(j, int(rng.integers(0, 150))) for j in edge]
+    cells += [(int(rng.integers(0, 130)), int(rng.integers(0, 150))) for _ in range(10)]
+    scale = np.max(np.abs(g))
+    for (j, i) in cells:
+        for v in range(U.shape[0]):
+            e = np.zeros_like(U)
+            e[v, j, i] = 1.0
+            _, jv = orc.rhs_jvp(prob, U, e)
+            ref = float(np.sum(w * jv))
+            den = max(abs(ref), 1e-3 * scale)
+
+            def kappa():
+                k = 0.0
+                for _ in range(3):
+                    Up = U * (1.0 + 2.220446049250313e-16 * prng.choice([-1.0, 0.0, 1.0], size=U.shape))
+                    _, jv2 = orc.rhs_jvp(prob, Up, e)
+                    k = max(k, abs(float(np.sum(w * jv2)) - ref))
+                return k / den
+
+            err = abs(g[v, j, i] - ref)
+            if err > 1e-10 * den:
+                parity_log.bar(err, den, 1e-10, kappa, f"(J^T w) entry {v},{j},{i} 2D mixed", cap=1e-7)
+
+
+def test_vjp_hybrid_off_full_transposed_jacobian():
+    """With the hybrid switch off every face takes the WENO flux: the
+    linear-upwind pass takes no face and flags every tile."""
+    prob, U = P.random_state(2, [9, 8], seed=5, kind="mixed")
+    prob["hybrid"] = 0
+    rng = np.random.default_rng(6)
+    w = rng.normal(size=U.shape)
+    g = _vjp(prob, U, w)
+    ref = np.zeros(U.size)
+    for k in range(U.size):
+        e = np.zeros(U.size)
+        e[k] = 1.0
+        _, jv = orc.rhs_jvp(prob, U, e.reshape(U.shape))
+        ref[k] = np.sum(w * jv)
+    assert np.allclose(g.reshape(-1), ref, rtol=1e-10, atol=1e-11 * np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind,hybrid", [("mixed", 1), ("smooth", 0), ("jumps", 1)])
+def test_vjp_tiling_on_a_replicated_state(precision, kind, hybrid):
+    """A periodic 30 x 26 state and cotangent repeated 5 x 5 times on a
+    150 x 130 periodic grid with the same spacing: the gradient repeats too.
+    The large grid has several tiles per line (59 cells along x; along y 59
+    cells in FP64 and 8 x-adjacent lines of 27 cells in FP32, ragged at the
+    end), the small one a single tile per line, and the two passes split the
+    faces the same way on both.  A cell at least 3 cells from the small
+    grid's edges receives the same face contributions in the same order on
+    both grids, so it agrees bitwise; the other cells receive their
+    periodic-ghost contributions in another order and agree to rounding."""
+    prob, U = P.random_state(2, [30, 26], seed=17, kind=kind)
+    prob["hybrid"] = hybrid
+    big = dict(prob, n=[150, 130], hi=[5.0, 5.0])
+    rng = np.random.default_rng(12)
+    w = rng.normal(size=U.shape)
+    g_small = _vjp(prob, U, w, precision)
+    g_big = _vjp(big, np.tile(U, (1, 5, 5)), np.tile(w, (1, 5, 5)), precision)
+    rep = np.tile(g_small, (1, 5, 5))
+    inner = np.zeros(g_small.shape[1:], dtype=bool)
+    inner[3:-3, 3:-3] = True
+    inner = np.tile(inner, (5, 5))
+    assert np.array_equal(g_big[:, inner], rep[:, inner])
+    tol = (1e-5 if precision == "fp32" else 1e-12) * np.max(np.abs(g_small))
+    assert np.max(np.abs(g_big - rep)) <= tol
