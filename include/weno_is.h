@@ -211,7 +211,8 @@ weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t fl
  * faces of the line-after-line face sequence (a tile may end one line and
  * start the next; lines shorter than 122 cells take variant 3), 6: flat
  * with 251 faces on 256 threads (lines shorter than 250 take 3).  Defaults:
- * FP64 5 in every direction; FP32 and mixed 3 along x, 1 across.
+ * FP64 5 in every direction except along y in 3D (2); FP32 and mixed 3
+ * along x, 1 across.
  * variants[3] (if not NULL) receives the choice per direction.
  * The state is not changed; the step graphs are rebuilt on next use.
  * Synchronizes. */

@@ -43,15 +43,15 @@ namespace wis {
 
 template <typename T> __device__ __forceinline__ T sgn(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
 
-// record bars of one cell (NQ entries, same layout as CellLayout) -> dU
+// record bars of one cell (NQ entries, same layout as CellLayout) -> dU;
+// isq = 1/sqrt(rho) and ic = 1/c as cell_prepare computed them
 template <typename T, int DIM, int DIR>
-__device__ __forceinline__ void cell_adj(const T* U, T gamma, const T* qb, T* Ub)
+__device__ __forceinline__ void cell_adj(const T* U, T gamma, T isq, T ic, const T* qb, T* Ub)
 {
     using CL = CellLayout<DIM>;
     constexpr int NV = DIM + 2;
     const T gm1 = gamma - T(1);
     const T rho = U[0];
-    const T isq = Ar<T>::rsqrt_(rho);
     const T irho = isq * isq;
     T m2 = T(0);
 #pragma unroll
@@ -59,8 +59,7 @@ __device__ __forceinline__ void cell_adj(const T* U, T gamma, const T* qb, T* Ub
     const T E = U[DIM + 1];
     const T p = gm1 * fmaT(T(-0.5) * irho, m2, E);
     const T c2 = gamma * p * irho;
-    const T ic = Ar<T>::rsqrt_(c2);   // 1/c; c as in the forward record
-    const T c = c2 * ic;
+    const T c = c2 * ic;   // as in the forward record
     const T un = U[1 + DIR] * irho;
     const T Ep = E + p;
 
@@ -332,7 +331,7 @@ struct VjpSmem {
     static constexpr int NRB = DIM + 2;
     static constexpr int NFB = NUFF + 2 * NRB + 3;
     static constexpr size_t bytes =
-        sizeof(T) * ((size_t)NQ * LNC + (size_t)NV * LNC + (size_t)LNF * NFB) + sizeof(int) * (size_t)LNF;
+        sizeof(T) * ((size_t)(NQ + 2) * LNC + (size_t)NV * LNC + (size_t)LNF * NFB) + sizeof(int) * (size_t)LNF;
 };
 
 // Residency of the WENO pass: its per-face reverse needs more than 255
@@ -356,8 +355,8 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
     constexpr int LINES = SM::LINES, LNF = SM::LNF, LNC = SM::LNC;
     constexpr int NT = VjpTile<T, DIM, DIR>::NT;
     constexpr int NUF = SM::NUF, NUFF = SM::NUFF, NRB = SM::NRB;
-    T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ][NC][LINES] cell records
-    T* wq = cq + NQ * LNC;                    // [NV][NC][LINES] cotangent
+    T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ + 2][NC][LINES] cell records, 1/sqrt(rho), 1/c
+    T* wq = cq + (NQ + 2) * LNC;              // [NV][NC][LINES] cotangent
     T* UF = wq + NV * LNC;                    // [NF][LINES][NUFF] U and F bars (see below)
     T* RB = UF + LNF * NUFF;                  // [NF][LINES][2][NRB] Roe-field bars of cells 2 and 3
     T* SP = RB + LNF * 2 * NRB;               // [NF][LINES][3] LLF speed bars
@@ -394,10 +393,12 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
             const long long g = base0 + l + (long long)cell * sd;
 #pragma unroll
             for (int v = 0; v < NV; ++v) wq[v * LNC + idx] = inside ? Wg[g + v * a.sv] : T(0);
-            T q[NQ];
-            cell_prepare<T, DIM, DIR>(U, gamma, q);
+            T q[NQ], inv[2];
+            cell_prepare<T, DIM, DIR>(U, gamma, q, inv);
 #pragma unroll
             for (int kk = 0; kk < NQ; ++kk) cq[kk * LNC + idx] = q[kk];
+            cq[NQ * LNC + idx] = inv[0];
+            cq[(NQ + 1) * LNC + idx] = inv[1];
         } else {
 #pragma unroll
             for (int v = 0; v < NV; ++v) wq[v * LNC + idx] = T(0);
@@ -648,7 +649,7 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
         T U[NV], Ub[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) U[v] = cq[(CL::U + v) * LNC + pc * LINES + l];
-        cell_adj<T, DIM, DIR>(U, gamma, qb, Ub);
+        cell_adj<T, DIM, DIR>(U, gamma, cq[NQ * LNC + pc * LINES + l], cq[(NQ + 1) * LNC + pc * LINES + l], qb, Ub);
         if (owned) {
             const long long g = base0 + l + (long long)cell * sd;
 #pragma unroll

@@ -86,9 +86,10 @@ template <int DIM> struct CellLayout {
 };
 
 // Primitives, physical flux along DIR and |eigenvalues| of one cell
-// (Eq. goveq4; E = p/(gamma-1) + rho |u|^2/2).  q[k] receives record entry k.
+// (Eq. goveq4; E = p/(gamma-1) + rho |u|^2/2).  q[k] receives record entry k;
+// inv (if not null) receives 1/sqrt(rho) and 1/c.
 template <typename T, int DIM, int DIR>
-__device__ __forceinline__ void cell_prepare(const T* U, T gamma, T* q)
+__device__ __forceinline__ void cell_prepare(const T* U, T gamma, T* q, T* inv = nullptr)
 {
     using CL = CellLayout<DIM>;
     const T gm1 = gamma - T(1);
@@ -101,7 +102,9 @@ __device__ __forceinline__ void cell_prepare(const T* U, T gamma, T* q)
     const T E = U[DIM + 1];
     const T p = gm1 * fmaT(T(-0.5) * irho, m2, E);
     const T c2 = gamma * p * irho;
-    const T c = c2 * Ar<T>::rsqrt_(c2);   // sqrt(c2) without the correctly rounded sqrt sequence
+    const T ic = Ar<T>::rsqrt_(c2);
+    const T c = c2 * ic;   // sqrt(c2) without the correctly rounded sqrt sequence
+    if (inv != nullptr) { inv[0] = isq; inv[1] = ic; }
     const T un = U[1 + DIR] * irho;
     const T Ep = E + p;
 #pragma unroll
