@@ -127,10 +127,14 @@ void weno_destroy(weno_ctx* ctx);
 
 /* Copy a state into the context and set the time to t (steps counter and
  * device status are reset).  U: interior-only array (see conventions), host
- * memory when on_device = 0, device memory otherwise. */
+ * memory when on_device = 0, device memory otherwise.  Page-locked, mapped
+ * host memory (cudaHostAlloc, or registered with the mapped flag) is read
+ * directly by the layout kernel; pageable host memory goes through a device
+ * copy.  Synchronizes the context's stream. */
 weno_status weno_set_state(weno_ctx* ctx, const void* U, int on_device, double t);
 
 /* Copy the current state out (same layout) and, if t is not NULL, the time.
+ * Page-locked, mapped host memory is written directly by the layout kernel.
  * Synchronizes the context's stream. */
 weno_status weno_get_state(weno_ctx* ctx, void* U, int on_device, double* t);
 

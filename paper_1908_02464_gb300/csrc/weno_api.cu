@@ -465,16 +465,33 @@ static weno_status ensure_stage_io(weno_ctx* ctx)
     return WENO_OK;
 }
 
+// Device address of a page-locked, mapped host buffer (cudaHostAlloc, or
+// cudaHostRegister with the mapped flag), else null: the layout copy can
+// then read or write it directly over the host link, one kernel for the
+// transfer and the layout change.  Pageable memory goes through a copy.
+static void* mapped_host(const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 weno_status weno_set_state(weno_ctx* ctx, const void* U, int on_device, double t)
 {
     if (!ctx || !U) return WENO_ERR_INVALID_ARG;
     const size_t bytes = interior_cells(ctx) * ctx->nv * ctx->esz;
     const void* src = U;
     if (!on_device) {
-        weno_status st = ensure_stage_io(ctx);
-        if (st != WENO_OK) return st;
-        CK(cudaMemcpyAsync(ctx->stage_io, U, bytes, cudaMemcpyHostToDevice, ctx->stream));
-        src = ctx->stage_io;
+        src = mapped_host(U);
+        if (src == nullptr) {
+            weno_status st = ensure_stage_io(ctx);
+            if (st != WENO_OK) return st;
+            CK(cudaMemcpyAsync(ctx->stage_io, U, bytes, cudaMemcpyHostToDevice, ctx->stream));
+            src = ctx->stage_io;
+        }
     }
     CK(do_pack(ctx, src, ctx->buf[0], 1, ctx->stream));
     std::memset(ctx->tm_host, 0, sizeof(DevTime));
@@ -494,6 +511,8 @@ weno_status weno_get_state(weno_ctx* ctx, void* U, int on_device, double* t)
     const size_t bytes = interior_cells(ctx) * ctx->nv * ctx->esz;
     if (on_device) {
         CK(do_pack(ctx, ctx->buf[ctx->phase], U, 0, ctx->stream));
+    } else if (void* dst = mapped_host(U)) {
+        CK(do_pack(ctx, ctx->buf[ctx->phase], dst, 0, ctx->stream));
     } else {
         st = ensure_stage_io(ctx);
         if (st != WENO_OK) return st;

@@ -157,3 +157,40 @@ def test_switch_threshold_flags_are_nested_in_the_characteristic_length():
             mism = np.nonzero(flags != oflags)[0]
             assert np.all(np.abs(ratio[mism] - 1.0) < 1e-9), len(mism)
     assert counts[-1] > counts[0], counts
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["sod", "dmr", "vortex"])
+def test_host_state_transfer_paths_agree(precision, case):
+    """weno_set_state / weno_get_state with pageable host memory (numpy; a
+    copy through a device buffer), page-locked host memory (torch pinned; the
+    layout kernel reads and writes it directly) and device memory give the
+    same states bitwise, and so do the steps that follow."""
+    if case == "sod":
+        prob, U = P.sod(300)
+    elif case == "dmr":
+        prob, U = P.double_mach(130, 40)
+    else:
+        prob, U = P.vortex3d(20)
+    np_dtype = np.float64 if precision == "fp64" else np.float32
+    tdtype = torch.float64 if precision == "fp64" else torch.float32
+    U = U.astype(np_dtype)
+    sources = {"pageable": U, "pinned": torch.from_numpy(U).pin_memory(), "device": torch.from_numpy(U).cuda()}
+    outs = {}
+    for name, src in sources.items():
+        s = weno.Solver(prob, precision)
+        s.set_state(src, 0.0)
+        back = {"pageable": np.empty_like(U), "pinned": torch.empty(U.shape, dtype=tdtype).pin_memory(),
+                "device": torch.empty(U.shape, dtype=tdtype, device="cuda")}
+        for kind, dst in back.items():
+            t = weno.weno_get_state(s.ctx, dst)
+            got = dst if isinstance(dst, np.ndarray) else dst.cpu().numpy()
+            assert t == 0.0 and np.array_equal(got, U), (name, kind)
+        s.advance(1.0, max_steps=3)
+        V = torch.empty(U.shape, dtype=tdtype).pin_memory()
+        weno.weno_get_state(s.ctx, V)
+        W, _ = s.get_state()
+        assert np.array_equal(V.numpy(), W)
+        outs[name] = W
+        s.close()
+    assert np.array_equal(outs["pageable"], outs["pinned"]) and np.array_equal(outs["pageable"], outs["device"])
