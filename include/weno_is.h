@@ -398,11 +398,12 @@ const char* weno_last_error(const weno_ctx* ctx);
 weno_status weno_measure_fma_peak(int precision, double* flops, double* seconds);
 
 /* Diagnostic (no counterpart in the paper): evaluates, for n doubles x_dev[i]
- * on the device, the Newton-refined reciprocal that the FP64 sweeps use (Roe
- * average, weight denominator of Eq. eq8-r) next to CUDA's correctly rounded
- * 1.0 / x, so that tests can bound its error.  out_dev (device, 2 n doubles,
- * caller-owned) receives [rcp_newton(x) | 1/x].  n < 0, or null pointers
- * with n > 0: WENO_ERR_INVALID_ARG.  Synchronizes the device. */
+ * on the device, the refined reciprocal and reciprocal square root that the
+ * FP64 sweeps use (Roe average, sound speeds, weight denominator of Eq.
+ * eq8-r) next to CUDA's correctly rounded 1.0 / x and its rsqrt(x), so that
+ * tests can bound their errors.  out_dev (device, 4 n doubles, caller-owned)
+ * receives [rcp_newton(x) | 1/x | rsqrt_refined(x) | rsqrt(x)].  n < 0, or
+ * null pointers with n > 0: WENO_ERR_INVALID_ARG.  Synchronizes the device. */
 weno_status weno_arith_selftest(const double* x_dev, long long n, double* out_dev);
 
 #ifdef __cplusplus

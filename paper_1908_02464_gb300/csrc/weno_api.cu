@@ -41,6 +41,11 @@ struct weno_ctx {
     double dx[3] = {1, 1, 1}, inv_dx[3] = {1, 1, 1}, eps_h[3] = {0, 0, 0};
     void* buf[3] = {nullptr, nullptr, nullptr};
     void* acc = nullptr;
+    // primitives (cell_prims) of the interior cells of a stage's state: the
+    // first sweep of a stage computes and stores them, the other directions
+    // read them (multi-dimensional FP64 only, see use_prims)
+    void* prim = nullptr;
+    bool use_prims = false;
     void* rhs_in = nullptr;
     void* rhs_out = nullptr;
     void* stage_io = nullptr;   // interior-size staging for host copies
@@ -127,7 +132,25 @@ static wis::SweepArgs sweep_args(weno_ctx* c, int dir)
     a.dx0 = c->dx[0];
     a.lo1 = c->g.lo[1];
     a.dx1 = c->dx[1];
+    a.acc_scale = 1.0;
+    a.acc_scale_f = 1.0f;
+    // a stage sweeps the directions from the last to x: the first one
+    // computes and stores the primitives, the others read them
+    if (c->use_prims) {
+        if (dir == c->dim - 1) a.Pout = c->prim;
+        else a.P = c->prim;
+    }
     return a;
+}
+
+// the sweep at position i of a stage (directions from the last to x) reads
+// the accumulator of the sweeps before it: unscaled after the first one
+// (MODE_ACC_SET), scaled after an accumulating one
+static void set_acc_scale(weno_ctx* c, wis::SweepArgs& a, int i)
+{
+    const double s = i == 1 ? c->inv_dx[c->dim - 1] * (1.0 / 60.0) : 1.0;
+    a.acc_scale = s;
+    a.acc_scale_f = (float)s;
 }
 
 static void set_rk(wis::SweepArgs& a, double ra, double rb)
@@ -188,6 +211,7 @@ static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* ou
     for (int i = 0; i < c->dim; ++i) {
         const int d = c->dim - 1 - i;
         wis::SweepArgs a = sweep_args(c, d);
+        set_acc_scale(c, a, i);
         a.U = in;
         a.tm = c->tm;
         a.stage = stage;
@@ -289,6 +313,7 @@ static void free_all(weno_ctx* c)
         if (c->buf[k]) cudaFree(c->buf[k]);
     }
     if (c->acc) cudaFree(c->acc);
+    if (c->prim) cudaFree(c->prim);
     if (c->rhs_in) cudaFree(c->rhs_in);
     if (c->rhs_out) cudaFree(c->rhs_out);
     if (c->stage_io) cudaFree(c->stage_io);
@@ -407,6 +432,16 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
         e = cudaMalloc(&ctx->buf[k], bytes);
         if (e == cudaSuccess) e = cudaMemset(ctx->buf[k], 0, bytes);
     }
+    // FP64 multi-dimensional grids: the square roots and reciprocals of a
+    // cell's primitives cost about 30 FP64 instructions; they are computed
+    // once per stage (first sweep) instead of once per direction.  The buffer
+    // serves the ghosted layout of the steps and the plain one of weno_rhs.
+    ctx->use_prims = ctx->prec == WENO_FP64 && dim > 1;
+    if (e == cudaSuccess && ctx->use_prims) {
+        const size_t pbytes = (size_t)ctx->sv * (dim + 5) * ctx->esz;
+        e = cudaMalloc(&ctx->prim, pbytes);
+        if (e == cudaSuccess) e = cudaMemset(ctx->prim, 0, pbytes);
+    }
     if (e == cudaSuccess && dim > 1) {
         e = cudaMalloc(&ctx->acc, bytes);
         if (e == cudaSuccess) e = cudaMemset(ctx->acc, 0, bytes);
@@ -431,7 +466,7 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
         return WENO_ERR_CUDA;
     }
     std::memset(ctx->tm_host, 0, sizeof(DevTime));
-    // default tiles, measured measured on the 2048 x 512 double Mach reflection: FP64 flat
+    // default tiles, measured on the 2048 x 512 double Mach reflection: FP64 flat
     // 128-face tiles (ALU bound, every lane busy), FP32 1 x 127 along x and
     // 8 x 15 across (coalesced rows); weno_autotune refines them per state
     // FP64: flat tiles, except along y in 3D, where 4 x-adjacent lines per
@@ -588,6 +623,7 @@ static weno_status issue_rhs(weno_ctx* ctx, const void* U, void* out, double t, 
     for (int i = 0; i < ctx->dim; ++i) {
         const int d = ctx->dim - 1 - i;
         wis::SweepArgs a = sweep_args(ctx, d);
+        set_acc_scale(ctx, a, i);
         a.sy = sy; a.sz = sz; a.sv = sv; a.off0 = 0;
         a.U = U;
         a.xs_fixed = wis::dmr_shock_x(t);
@@ -795,6 +831,18 @@ static weno_status prepare_timing(weno_ctx* ctx)
     if (ctx->dim == 1 && (st = ensure_rhs_bufs(ctx)) != WENO_OK) return st;
     void* cur = ctx->buf[ctx->phase];
     if (ctx->p.splitting == wis::SPLIT_LF) CK(issue_lf(ctx, cur, 3, nullptr, ctx->stream));
+    if (ctx->use_prims) {
+        // the sweeps timed alone along the other directions read the
+        // primitives that the first direction's sweep stores
+        const int d = ctx->dim - 1;
+        wis::SweepArgs a = sweep_args(ctx, d);
+        a.U = cur;
+        a.xs_fixed = wis::dmr_shock_x(ctx->tm_host->t);
+        a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
+        a.mode = wis::MODE_ACC_SET;
+        a.acc = ctx->acc;
+        CK(do_sweep(ctx, d, a, ctx->stream));
+    }
     return WENO_OK;
 }
 
@@ -973,6 +1021,8 @@ __global__ void k_arith_selftest(const double* x, long long n, double* out)
         const double v = x[i];
         out[i] = wis::rcp_newton(v);
         out[n + i] = 1.0 / v;
+        out[2 * n + i] = wis::rsqrt_refined(v);
+        out[3 * n + i] = rsqrt(v);
     }
 }
 

@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(Batch2Tile<V>::NT) k_batch2d(BatchArgs b)
         ay.acc = acc;
         ax.mode = MODE_COMBINE;
         ax.acc = acc;
+        ax.acc_scale = ay.inv_dx * (1.0 / 60.0);   // the y-sweep stores unscaled flux differences
+        ax.acc_scale_f = (float)ax.acc_scale;
         const T inv_dx_t[2] = {T(ax.inv_dx), T(ay.inv_dx)};
         const int nsx = (nx + BT::XS - 1) / BT::XS, nlx = (ny + BT::XL - 1) / BT::XL;
         const int nsy = (ny + BT::YS - 1) / BT::YS, nly = (nx + BT::YL - 1) / BT::YL;

@@ -3,8 +3,9 @@
 // Everything here is a __device__ __forceinline__ routine used by the sweep
 // kernels in weno_kernels.cuh.  The order of operations follows the paper
 // (Zhu & Hu, arXiv 1908.02464):
-//   cell_prepare   primitives, physical flux, |eigenvalues| of one cell
-//                  (Eq. goveq4 and its multi-D form)
+//   cell_prims     direction-independent primitives of one cell
+//   cell_record    physical flux and |eigenvalues| along the sweep from them
+//   cell_prepare   both (Eq. goveq4 and its multi-D form)
 //   roe_state      Roe average at x_{j+1/2} (Sec. 2.4 step (1))
 //   proj_all       L^s . x for every field s (Sec. 2.4 step (2)-(3),
 //                  Eq. eqchara), written from the structure of L instead of a
@@ -38,26 +39,40 @@ __device__ __forceinline__ float absT(float a) { return fabsf(a); }
 
 template <typename T> struct Ar;
 
-// Reciprocal refined by Newton's method from the hardware's approximate value
-// (rcp.approx): x <- x (2 - d x) squares the relative error of the estimate
-// at each step, so two steps reach double precision up to the rounding of
-// the last one.  For the finite, positive, normal arguments of the sweeps
-// (sums of square roots of densities, weight denominators).
+// Reciprocal from the hardware's approximate value (rcp.approx) refined by
+// one third-order step of the series 1/d = x / (1 - e) = x (1 + e + e^2 +
+// ...), e = 1 - d x (Householder's method of order 3): the seed's relative
+// error e becomes about e^3, far below double rounding, so the result is
+// within one ulp.  Three FMAs.  For the finite, positive, normal arguments
+// of the sweeps (sums of square roots of densities, weight denominators).
 __device__ __forceinline__ double rcp_newton(double d)
 {
     double x;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x) : "d"(d));
-    double e = __fma_rn(-d, x, 1.0);   // 1 - d x
-    x = __fma_rn(x, e, x);             // x + x (1 - d x)
-    e = __fma_rn(-d, x, 1.0);
-    return __fma_rn(x, e, x);
+    const double e = __fma_rn(-d, x, 1.0);   // 1 - d x
+    return __fma_rn(x, __fma_rn(e, e, e), x);
+}
+
+// 1/sqrt(x) from the hardware's approximate value (rsqrt.approx) refined by
+// one third-order step of the binomial series (1 - e)^(-1/2) = 1 + e/2 +
+// 3 e^2 / 8 + ..., e = 1 - x r^2 (Householder's method of order 3): the
+// seed's error leaves a term of about (5/16) e^3.  Two products and three
+// FMAs.  For finite, positive, normal x; zero, negative and non-finite
+// arguments give NaN (the admissibility checks reject those states).
+__device__ __forceinline__ double rsqrt_refined(double x)
+{
+    double r;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    const double e = __fma_rn(-x, __dmul_rn(r, r), 1.0);
+    const double q = __fma_rn(e, 0.375, 0.5);
+    return __fma_rn(__dmul_rn(r, e), q, r);
 }
 
 template <> struct Ar<double> {
     static __device__ __forceinline__ double rcp_f(double x) { return rcp_newton(x); }
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt_refined(x); }
 };
 
 template <> struct Ar<float> {
@@ -85,42 +100,92 @@ template <int DIM> struct CellLayout {
     static constexpr int NQ = SH + 5;
 };
 
-// Primitives, physical flux along DIR and |eigenvalues| of one cell
-// (Eq. goveq4; E = p/(gamma-1) + rho |u|^2/2).  q[k] receives record entry k;
-// inv (if not null) receives 1/sqrt(rho) and 1/c.
-template <typename T, int DIM, int DIR>
-__device__ __forceinline__ void cell_prepare(const T* U, T gamma, T* q, T* inv = nullptr)
+// Direction-independent primitives of one cell (NP entries): 1/rho, p, c,
+// sqrt(rho) u[DIM], sqrt(rho) H, sqrt(rho).  They are the part of a cell
+// record that costs square roots and reciprocals.  The grid solver computes
+// them once per cell and Runge-Kutta stage, in the epilogue of the sweep
+// that writes the stage's state, and every sweep of the next stage reads
+// them instead of recomputing them per direction.
+template <int DIM> struct PrimLayout {
+    static constexpr int IRHO = 0;
+    static constexpr int P = 1;
+    static constexpr int C = 2;
+    static constexpr int SU = 3;            // sqrt(rho) u[DIM]
+    static constexpr int SH = 3 + DIM;      // sqrt(rho) H
+    static constexpr int SQ = 4 + DIM;      // sqrt(rho)
+    static constexpr int NP = 5 + DIM;
+};
+
+// Products that the compiler must not fuse with a neighbouring sum into a
+// multiply-add.  The cell primitives are computed in several kernels (the
+// tile staging, the Runge-Kutta epilogue, k_prims) and read back from memory
+// in others; with every product rounded on its own and every fused
+// multiply-add written out, all of them give the same bits.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+// Primitives of one cell (Eq. goveq4; E = p/(gamma-1) + rho |u|^2/2) into
+// P[NP]; inv (if not null) receives 1/sqrt(rho) and 1/c.
+template <typename T, int DIM>
+__device__ __forceinline__ void cell_prims(const T* U, T gamma, T* P, T* inv = nullptr)
 {
-    using CL = CellLayout<DIM>;
+    using PL = PrimLayout<DIM>;
     const T gm1 = gamma - T(1);
     const T rho = U[0];
     const T isq = Ar<T>::rsqrt_(rho);   // 1/sqrt(rho)
-    const T irho = isq * isq;
+    const T irho = mul_rn(isq, isq);
     T m2 = T(0);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) m2 = fmaT(U[1 + k], U[1 + k], m2);
     const T E = U[DIM + 1];
-    const T p = gm1 * fmaT(T(-0.5) * irho, m2, E);
-    const T c2 = gamma * p * irho;
+    const T p = mul_rn(gm1, fmaT(mul_rn(T(-0.5), irho), m2, E));
+    const T c2 = mul_rn(mul_rn(gamma, p), irho);
     const T ic = Ar<T>::rsqrt_(c2);
-    const T c = c2 * ic;   // sqrt(c2) without the correctly rounded sqrt sequence
+    const T c = mul_rn(c2, ic);   // sqrt(c2) without the correctly rounded sqrt sequence
     if (inv != nullptr) { inv[0] = isq; inv[1] = ic; }
-    const T un = U[1 + DIR] * irho;
-    const T Ep = E + p;
+    P[PL::IRHO] = irho;
+    P[PL::P] = p;
+    P[PL::C] = c;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) P[PL::SU + k] = mul_rn(U[1 + k], isq);
+    P[PL::SH] = mul_rn(E + p, isq);
+    P[PL::SQ] = mul_rn(rho, isq);
+}
+
+// Cell record for a sweep along DIR (physical flux, |eigenvalues|) from the
+// state U and its primitives P.
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void cell_record(const T* U, const T* P, T* q)
+{
+    using CL = CellLayout<DIM>;
+    using PL = PrimLayout<DIM>;
+    const T p = P[PL::P], c = P[PL::C];
+    const T un = mul_rn(U[1 + DIR], P[PL::IRHO]);
+    const T Ep = U[DIM + 1] + p;
 #pragma unroll
     for (int v = 0; v < CL::NV; ++v) q[CL::U + v] = U[v];
     q[CL::F + 0] = U[1 + DIR];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) q[CL::F + 1 + k] = U[1 + k] * un;
-    q[CL::F + 1 + DIR] += p;
-    q[CL::F + DIM + 1] = Ep * un;
+    for (int k = 0; k < DIM; ++k) q[CL::F + 1 + k] = k == DIR ? fmaT(U[1 + k], un, p) : mul_rn(U[1 + k], un);
+    q[CL::F + DIM + 1] = mul_rn(Ep, un);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) q[CL::SU + k] = U[1 + k] * isq;
-    q[CL::SH] = Ep * isq;
-    q[CL::SQ] = rho * isq;
+    for (int k = 0; k < DIM; ++k) q[CL::SU + k] = P[PL::SU + k];
+    q[CL::SH] = P[PL::SH];
+    q[CL::SQ] = P[PL::SQ];
     q[CL::LM] = absT(un - c);
     q[CL::L0] = absT(un);
     q[CL::LP] = absT(un + c);
+}
+
+// Primitives, physical flux and |eigenvalues| of one cell: the record of
+// cell_record from the primitives of cell_prims.  q[k] receives record
+// entry k; inv (if not null) receives 1/sqrt(rho) and 1/c.
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void cell_prepare(const T* U, T gamma, T* q, T* inv = nullptr)
+{
+    T P[PrimLayout<DIM>::NP];
+    cell_prims<T, DIM>(U, gamma, P, inv);
+    cell_record<T, DIM, DIR>(U, P, q);
 }
 
 // ----------------------------------------------------------------- Roe state

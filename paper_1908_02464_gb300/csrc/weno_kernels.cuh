@@ -104,6 +104,18 @@ struct SweepArgs {
     double lo0, dx0, lo1, dx1;   // x and y geometry (double Mach, jet)
     int stage;                   // RK stage (index of tm->xs_top)
     double xs_fixed;             // double Mach shock position when tm is null
+    // Primitives (cell_prims) of U's interior cells in U's layout, one plane
+    // of sv elements per entry.  P: read them (the first sweep of the stage
+    // wrote them); Pout: the tiles compute them and store those of their own
+    // cells; both null: the tiles compute them and keep them to themselves.
+    const void* P = nullptr;
+    void* Pout = nullptr;
+    // Scale of the accumulator `acc` as this sweep reads it (ACC_ADD, RHS,
+    // COMBINE): MODE_ACC_SET stores the plain difference of the (times 60)
+    // face fluxes, so its reader multiplies by that direction's 1/(60 dx);
+    // an ACC_ADD accumulator is already scaled (1).
+    double acc_scale = 1.0;
+    float acc_scale_f = 1.0f;
 };
 
 template <typename T> __device__ __forceinline__ T pick(double d, float f);
@@ -116,20 +128,21 @@ enum { BC_TRANSMISSIVE = 0, BC_REFLECT = 1, BC_PERIODIC = 2, BC_INFLOW = 3, BC_D
 // half width of the inflow jet (bc_state[0] where y < JET_HALF_WIDTH)
 constexpr double JET_HALF_WIDTH = 0.05;
 
-// State of cell `along` of a grid line (interior or one of the three ghost
-// cells per side), applying the boundary condition of direction DIR:
-// transmissive (nearest interior cell), reflecting (mirror, normal momentum
-// negated), periodic (wrap), fixed states (inflow, double Mach bottom and
-// top, jet).  `line` indexes the grid line: the row j for x sweeps, the
-// column i for y/z sweeps.
-template <typename T, int DIM, int DIR>
-__device__ __forceinline__ void stage_cell(const SweepArgs& a, const T* Ug, long long line_base, int line, int along,
-                                           int nd, T* U)
+// Where the state of cell `along` of a grid line comes from (interior or
+// one of the three ghost cells per side), applying the boundary condition of
+// direction DIR: transmissive (nearest interior cell), reflecting (mirror,
+// normal momentum negated), periodic (wrap), fixed states (inflow, double
+// Mach bottom and top, jet).  `line` indexes the grid line: the row j for x
+// sweeps, the column i for y/z sweeps.  Returns the fixed state's index
+// (0 or 1) or -1 with the source cell's global index in g and whether its
+// normal momentum is negated in flip.
+template <int DIR>
+__device__ __forceinline__ int cell_source(const SweepArgs& a, long long line_base, int line, int along, int nd,
+                                           long long& g, bool& flip)
 {
-    constexpr int NV = DIM + 2;
     const long long sd = DIR == 0 ? 1LL : (DIR == 1 ? a.sy : a.sz);
     int src = along;
-    bool flip = false;
+    flip = false;
     if (along < 0 || along >= nd) {
         const int side = along < 0 ? 0 : 1;
         const int gl = side == 0 ? -along : along - nd + 1;
@@ -150,19 +163,73 @@ __device__ __forceinline__ void stage_cell(const SweepArgs& a, const T* Ug, long
             const double y = a.lo1 + (line + 0.5) * a.dx1;
             fixed = y < JET_HALF_WIDTH ? 0 : 1;
         }
-        if (fixed >= 0) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) U[v] = pick<T>(a.bc_state[fixed][v], a.bc_state_f[fixed][v]);
-            return;
-        }
+        if (fixed >= 0) return fixed;
         if (bc == BC_TRANSMISSIVE) src = side == 0 ? 0 : nd - 1;
         else if (bc == BC_REFLECT) { src = side == 0 ? gl - 1 : nd - gl; flip = true; }
         else src = side == 0 ? nd - gl : gl - 1;
     }
-    const long long g = line_base + (long long)src * sd;
+    g = line_base + (long long)src * sd;
+    return -1;
+}
+
+// State of cell `along` of a grid line (see cell_source).
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void stage_cell(const SweepArgs& a, const T* Ug, long long line_base, int line, int along,
+                                           int nd, T* U)
+{
+    constexpr int NV = DIM + 2;
+    long long g = 0;
+    bool flip = false;
+    const int fixed = cell_source<DIR>(a, line_base, line, along, nd, g, flip);
+    if (fixed >= 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = pick<T>(a.bc_state[fixed][v], a.bc_state_f[fixed][v]);
+        return;
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) U[v] = Ug[g + v * a.sv];
     if (flip) U[1 + DIR] = -U[1 + DIR];
+}
+
+// Cell record of cell `along` of a grid line (see cell_source).  Interior
+// and mirrored cells take their primitives from Pg when it is given
+// (reflection negates the normal momentum and sqrt(rho) u_n and leaves the
+// rest unchanged); otherwise they are computed, and stored to Pw when it is
+// given and the cell is one of the tile's own (`own`, never a ghost cell).
+// Fixed states compute theirs.
+template <typename T, int DIM, int DIR>
+__device__ __forceinline__ void stage_record(const SweepArgs& a, const T* Ug, const T* Pg, T* Pw, bool own,
+                                             long long line_base, int line, int along, int nd, T gamma, T* q)
+{
+    constexpr int NV = DIM + 2;
+    using PL = PrimLayout<DIM>;
+    long long g = 0;
+    bool flip = false;
+    const int fixed = cell_source<DIR>(a, line_base, line, along, nd, g, flip);
+    T U[NV], P[PL::NP];
+    if (fixed >= 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) U[v] = pick<T>(a.bc_state[fixed][v], a.bc_state_f[fixed][v]);
+        cell_prepare<T, DIM, DIR>(U, gamma, q);
+        return;
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) U[v] = Ug[g + v * a.sv];
+    if (Pg != nullptr) {
+#pragma unroll
+        for (int k = 0; k < PL::NP; ++k) P[k] = Pg[g + k * a.sv];
+    } else {
+        cell_prims<T, DIM>(U, gamma, P);
+        if (Pw != nullptr && own) {
+#pragma unroll
+            for (int k = 0; k < PL::NP; ++k) Pw[g + k * a.sv] = P[k];
+        }
+    }
+    if (flip) {
+        U[1 + DIR] = -U[1 + DIR];
+        P[PL::SU + DIR] = -P[PL::SU + DIR];
+    }
+    cell_record<T, DIM, DIR>(U, P, q);
 }
 
 template <typename T, int DIM>
@@ -306,9 +373,12 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
     if (threadIdx.x == 0) { qcount = 0; wcount = 0u; }
 
     // ---- stage the tile (cells c0-3 .. c0+SEG+2 of LINES lines) --------
-    auto put = [&](int idx, const T (&U)[NV]) {
-        T q[NQ];
-        cell_prepare<T, DIM, DIR>(U, gamma, q);
+    // Cell records from the state and the primitives of the stage (read, or
+    // computed and stored for the tile's own cells: those between two of its
+    // faces, as the divergence below takes them).
+    const T* Pg = reinterpret_cast<const T*>(a.P);
+    T* Pw = reinterpret_cast<T*>(a.Pout);
+    auto put = [&](int idx, const T (&q)[NQ]) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) cq[k * NCELL + idx] = q[k];
     };
@@ -316,11 +386,13 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
         const int nCA = nA + 5, nCB = nB > 0 ? nB + 5 : 0;
         for (int idx = threadIdx.x; idx < nCA + nCB; idx += NT) {
             const bool inA = idx < nCA;
+            const int i = (inA ? idx : idx - nCA) - 3;   // cell index relative to the piece's first face
+            const bool own = i >= 0 && i <= (inA ? nA : nB) - 2;
             int inplane;
             const long long base = flat_line(inA ? LA : LA + 1, inplane);
-            T U[NV];
-            stage_cell<T, DIM, DIR>(a, Ug, base, inplane, inA ? fA0 - 3 + idx : idx - nCA - 3, nd, U);
-            put(idx, U);
+            T q[NQ];
+            stage_record<T, DIM, DIR>(a, Ug, Pg, Pw, own, base, inplane, inA ? fA0 + i : i, nd, gamma, q);
+            put(idx, q);
         }
     } else if (c0 >= 3 && c0 + SEG + 3 <= nd) {
         // the whole halo is interior (uniform over the block)
@@ -332,10 +404,21 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             if (line < nline) {
                 const long long g =
                     a.off0 + (long long)line * sl + (long long)pb * sp + (long long)(c0 - 3 + p) * sd;
-                T U[NV];
+                T U[NV], P[PrimLayout<DIM>::NP], q[NQ];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) U[v] = Ug[g + v * a.sv];
-                put(idx, U);
+                if (Pg != nullptr) {
+#pragma unroll
+                    for (int k = 0; k < PrimLayout<DIM>::NP; ++k) P[k] = Pg[g + k * a.sv];
+                } else {
+                    cell_prims<T, DIM>(U, gamma, P);
+                    if (Pw != nullptr && p >= 3 && p < SEG + 3) {
+#pragma unroll
+                        for (int k = 0; k < PrimLayout<DIM>::NP; ++k) Pw[g + k * a.sv] = P[k];
+                    }
+                }
+                cell_record<T, DIM, DIR>(U, P, q);
+                put(idx, q);
             }
         }
     } else {
@@ -347,10 +430,11 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             const int line = line0 + l;
             const int along = c0 - 3 + p;
             if (line < nline && along < nd + 3) {
-                T U[NV];
-                stage_cell<T, DIM, DIR>(a, Ug, a.off0 + (long long)line * sl + (long long)pb * sp, line, along,
-                                        nd, U);
-                put(idx, U);
+                const bool own = p >= 3 && p < SEG + 3 && along < nd;
+                T q[NQ];
+                stage_record<T, DIM, DIR>(a, Ug, Pg, Pw, own, a.off0 + (long long)line * sl + (long long)pb * sp,
+                                          line, along, nd, gamma, q);
+                put(idx, q);
             }
         }
     }
@@ -590,6 +674,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
     T* accp = reinterpret_cast<T*>(a.acc);
     const T* Unp = reinterpret_cast<const T*>(a.Un);
     const T rka = pick<T>(a.rk_a, a.rk_a_f), rkb = pick<T>(a.rk_b, a.rk_b_f);
+    const T acs = pick<T>(a.acc_scale, a.acc_scale_f);
     bool bad = false;
     for (int idx = threadIdx.x; idx < LINES * SEG; idx += NT) {
         int l, p;
@@ -615,25 +700,29 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             fr_ = DIR == 0 ? fl + 1 : fl + LINES;
             cpos = p;
         }
+        if (a.mode == MODE_ACC_SET) {
+            // the flux difference unscaled: the sweep that reads the
+            // accumulator multiplies it by acc_scale
+#pragma unroll
+            for (int v = 0; v < NV; ++v) accp[g + v * a.sv] = fh[v * NFACE + fl] - fh[v * NFACE + fr_];
+            continue;
+        }
         T rv[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) rv[v] = (fh[v * NFACE + fl] - fh[v * NFACE + fr_]) * inv_dx;
-        if (a.mode == MODE_ACC_SET) {
+        if (a.mode == MODE_ACC_ADD) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) accp[g + v * a.sv] = rv[v];
-        } else if (a.mode == MODE_ACC_ADD) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) accp[g + v * a.sv] += rv[v];
+            for (int v = 0; v < NV; ++v) accp[g + v * a.sv] = fmaT(accp[g + v * a.sv], acs, rv[v]);
         } else if (a.mode == MODE_RHS) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) outp[g + v * a.sv] = (accp ? accp[g + v * a.sv] : T(0)) + rv[v];
+            for (int v = 0; v < NV; ++v) outp[g + v * a.sv] = accp ? fmaT(accp[g + v * a.sv], acs, rv[v]) : rv[v];
         } else {
             const int ci = FLAT ? cpos + 3 : cidx(l, cpos + 3);
             T nu[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 T tot = rv[v];
-                if (accp) tot += accp[g + v * a.sv];
+                if (accp) tot = fmaT(accp[g + v * a.sv], acs, tot);
                 T val = rkb * fmaT(dt, tot, cq[(CL::U + v) * NCELL + ci]);
                 if (rka != T(0)) val = fmaT(rka, Unp[g + v * a.sv], val);
                 nu[v] = val;

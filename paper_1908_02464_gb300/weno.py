@@ -227,11 +227,12 @@ def weno_measure_fma_peak(precision: int = 0):
 
 
 def weno_arith_selftest(x_dev):
-    """[rcp_newton(x), 1/x] of a float64 CUDA tensor as a (2, n) float64 CUDA
-    tensor (diagnostic of the sweep arithmetic)."""
+    """[rcp_newton(x), 1/x, rsqrt_refined(x), rsqrt(x)] of a float64 CUDA
+    tensor as a (4, n) float64 CUDA tensor (diagnostic of the sweep
+    arithmetic)."""
     import torch
     x = x_dev.contiguous()
-    out = torch.empty((2, x.numel()), dtype=torch.float64, device=x.device)
+    out = torch.empty((4, x.numel()), dtype=torch.float64, device=x.device)
     _check(load().weno_arith_selftest(_vp(_ptr(x)), int(x.numel()), _vp(_ptr(out))))
     return out
 
