@@ -394,7 +394,7 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
 #pragma unroll
             for (int v = 0; v < NV; ++v) wq[v * LNC + idx] = inside ? Wg[g + v * a.sv] : T(0);
             T q[NQ], inv[2];
-            cell_prepare<T, DIM, DIR>(U, gamma, q, inv);
+            cell_prepare<T, DIM, DIR>(U, gamma, gamma - T(1), q, inv);
 #pragma unroll
             for (int kk = 0; kk < NQ; ++kk) cq[kk * LNC + idx] = q[kk];
             cq[NQ * LNC + idx] = inv[0];
@@ -430,7 +430,7 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
 
         auto ga = [&](int kk) -> T { return rec(2, kk); };
         auto gb = [&](int kk) -> T { return rec(3, kk); };
-        const Roe<T, DIM> r = roe_state<T, DIM>(ga, gb, gamma);
+        const Roe<T, DIM> r = roe_state<T, DIM>(ga, gb, gamma - T(1));
         RoeBar<T, DIM> rb;
         zero(rb);
         T dU[NV];

@@ -438,7 +438,7 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
     // serves the ghosted layout of the steps and the plain one of weno_rhs.
     ctx->use_prims = ctx->prec == WENO_FP64 && dim > 1;
     if (e == cudaSuccess && ctx->use_prims) {
-        const size_t pbytes = (size_t)ctx->sv * (dim + 5) * ctx->esz;
+        const size_t pbytes = (size_t)ctx->sv * 8 * ctx->esz;   // PrimLayout::STRIDE values per cell
         e = cudaMalloc(&ctx->prim, pbytes);
         if (e == cudaSuccess) e = cudaMemset(ctx->prim, 0, pbytes);
     }

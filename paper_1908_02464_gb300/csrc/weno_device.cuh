@@ -37,6 +37,24 @@ __device__ __forceinline__ float maxT(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double absT(double a) { return fabs(a); }
 __device__ __forceinline__ float absT(float a) { return fabsf(a); }
 
+// x / 2 without the FP64 pipe: for a normal result the exponent field is
+// lowered by one on the integer pipes, which is exact; zero stays zero,
+// infinities and NaN stay as they are; results below the smallest normal
+// number (|x| < 2^-1021, never met by the quantities halved here) become a
+// zero of x's sign.  On GB300 a DMUL takes a slot of the narrow FP64 pipe
+// that bounds the sweeps, the few integer instructions do not.
+__device__ __forceinline__ double halve(double x)
+{
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned ex = (unsigned)hi & 0x7ff00000u;
+    int h, l = lo;
+    if (ex - 0x00200000u <= 0x7fc00000u) h = hi - 0x00100000;      // normal result
+    else if (ex == 0x7ff00000u) h = hi;                             // inf, NaN
+    else { h = hi & (int)0x80000000u; l = 0; }                      // zero, tiny
+    return __hiloint2double(h, l);
+}
+__device__ __forceinline__ float halve(float x) { return 0.5f * x; }
+
 template <typename T> struct Ar;
 
 // Reciprocal from the hardware's approximate value (rcp.approx) refined by
@@ -114,7 +132,60 @@ template <int DIM> struct PrimLayout {
     static constexpr int SH = 3 + DIM;      // sqrt(rho) H
     static constexpr int SQ = 4 + DIM;      // sqrt(rho)
     static constexpr int NP = 5 + DIM;
+    // stored per cell as one record of 8 values (64 bytes in FP64, the 2D
+    // record padded): a cell's primitives are two 32-byte sectors, written
+    // and read with 16-byte accesses
+    static constexpr int STRIDE = 8;
 };
+
+// the primitive record of cell g (PrimLayout::STRIDE values from P + STRIDE g)
+template <int DIM>
+__device__ __forceinline__ void load_prims(const double* P, long long g, double* out)
+{
+    const double2* p = reinterpret_cast<const double2*>(P + g * PrimLayout<DIM>::STRIDE);
+#pragma unroll
+    for (int j = 0; j < PrimLayout<DIM>::STRIDE / 2; ++j) {
+        const double2 v = __ldg(p + j);
+        if (2 * j < PrimLayout<DIM>::NP) out[2 * j] = v.x;
+        if (2 * j + 1 < PrimLayout<DIM>::NP) out[2 * j + 1] = v.y;
+    }
+}
+template <int DIM>
+__device__ __forceinline__ void load_prims(const float* P, long long g, float* out)
+{
+    const float4* p = reinterpret_cast<const float4*>(P + g * PrimLayout<DIM>::STRIDE);
+#pragma unroll
+    for (int j = 0; j < PrimLayout<DIM>::STRIDE / 4; ++j) {
+        const float4 v = __ldg(p + j);
+        const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (4 * j + k < PrimLayout<DIM>::NP) out[4 * j + k] = w[k];
+    }
+}
+template <int DIM>
+__device__ __forceinline__ void store_prims(double* P, long long g, const double* in)
+{
+    double2* p = reinterpret_cast<double2*>(P + g * PrimLayout<DIM>::STRIDE);
+#pragma unroll
+    for (int j = 0; j < PrimLayout<DIM>::STRIDE / 2; ++j) {
+        const double x = 2 * j < PrimLayout<DIM>::NP ? in[2 * j] : 0.0;
+        const double y = 2 * j + 1 < PrimLayout<DIM>::NP ? in[2 * j + 1] : 0.0;
+        p[j] = make_double2(x, y);
+    }
+}
+template <int DIM>
+__device__ __forceinline__ void store_prims(float* P, long long g, const float* in)
+{
+    float4* p = reinterpret_cast<float4*>(P + g * PrimLayout<DIM>::STRIDE);
+#pragma unroll
+    for (int j = 0; j < PrimLayout<DIM>::STRIDE / 4; ++j) {
+        float w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[k] = 4 * j + k < PrimLayout<DIM>::NP ? in[4 * j + k] : 0.0f;
+        p[j] = make_float4(w[0], w[1], w[2], w[3]);
+    }
+}
 
 // Products that the compiler must not fuse with a neighbouring sum into a
 // multiply-add.  The cell primitives are computed in several kernels (the
@@ -125,12 +196,11 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 
 // Primitives of one cell (Eq. goveq4; E = p/(gamma-1) + rho |u|^2/2) into
-// P[NP]; inv (if not null) receives 1/sqrt(rho) and 1/c.
+// P[NP], gm1 = gamma - 1; inv (if not null) receives 1/sqrt(rho) and 1/c.
 template <typename T, int DIM>
-__device__ __forceinline__ void cell_prims(const T* U, T gamma, T* P, T* inv = nullptr)
+__device__ __forceinline__ void cell_prims(const T* U, T gamma, T gm1, T* P, T* inv = nullptr)
 {
     using PL = PrimLayout<DIM>;
-    const T gm1 = gamma - T(1);
     const T rho = U[0];
     const T isq = Ar<T>::rsqrt_(rho);   // 1/sqrt(rho)
     const T irho = mul_rn(isq, isq);
@@ -138,7 +208,7 @@ __device__ __forceinline__ void cell_prims(const T* U, T gamma, T* P, T* inv = n
 #pragma unroll
     for (int k = 0; k < DIM; ++k) m2 = fmaT(U[1 + k], U[1 + k], m2);
     const T E = U[DIM + 1];
-    const T p = mul_rn(gm1, fmaT(mul_rn(T(-0.5), irho), m2, E));
+    const T p = mul_rn(gm1, fmaT(-halve(irho), m2, E));
     const T c2 = mul_rn(mul_rn(gamma, p), irho);
     const T ic = Ar<T>::rsqrt_(c2);
     const T c = mul_rn(c2, ic);   // sqrt(c2) without the correctly rounded sqrt sequence
@@ -181,10 +251,10 @@ __device__ __forceinline__ void cell_record(const T* U, const T* P, T* q)
 // cell_record from the primitives of cell_prims.  q[k] receives record
 // entry k; inv (if not null) receives 1/sqrt(rho) and 1/c.
 template <typename T, int DIM, int DIR>
-__device__ __forceinline__ void cell_prepare(const T* U, T gamma, T* q, T* inv = nullptr)
+__device__ __forceinline__ void cell_prepare(const T* U, T gamma, T gm1, T* q, T* inv = nullptr)
 {
     T P[PrimLayout<DIM>::NP];
-    cell_prims<T, DIM>(U, gamma, P, inv);
+    cell_prims<T, DIM>(U, gamma, gm1, P, inv);
     cell_record<T, DIM, DIR>(U, P, q);
 }
 
@@ -200,7 +270,7 @@ template <typename T, int DIM> struct Roe {
 // Roe average (Sec. 2.4 step (1)) between cells a (j) and b (j+1); get_a(k)
 // and get_b(k) read record entry k of the two cells.
 template <typename T, int DIM, typename GA, typename GB>
-__device__ __forceinline__ Roe<T, DIM> roe_state(GA get_a, GB get_b, T gamma)
+__device__ __forceinline__ Roe<T, DIM> roe_state(GA get_a, GB get_b, T gm1)
 {
     using CL = CellLayout<DIM>;
     Roe<T, DIM> r;
@@ -213,8 +283,7 @@ __device__ __forceinline__ Roe<T, DIM> roe_state(GA get_a, GB get_b, T gamma)
         q2 = fmaT(r.u[k], r.u[k], q2);
     }
     r.H = (get_a(CL::SH) + get_b(CL::SH)) * inv;
-    r.hq2 = T(0.5) * q2;
-    const T gm1 = gamma - T(1);
+    r.hq2 = halve(q2);
     const T c2 = gm1 * (r.H - r.hq2);
     r.ic = Ar<T>::rsqrt_(c2);
     r.c = c2 * r.ic;
@@ -251,7 +320,7 @@ __device__ __forceinline__ void proj_all(const Roe<T, DIM>& r, const T* x, T* w)
     for (int k = 1; k < DIM; ++k) dot = fmaT(r.u[k], x[1 + k], dot);
     const T t1 = r.b1 * (fmaT(r.hq2, x[0], x[DIM + 1]) - dot);
     const T a = fmaT(r.u[DIR], x[0], -x[1 + DIR]) * r.ic;
-    w[0] = T(0.5) * (t1 + a);
+    w[0] = halve(t1 + a);
     w[1] = x[0] - t1;
     int s = 2;
 #pragma unroll
@@ -260,7 +329,7 @@ __device__ __forceinline__ void proj_all(const Roe<T, DIM>& r, const T* x, T* w)
         w[s] = fmaT(-r.u[t], x[0], x[1 + t]);
         ++s;
     }
-    w[DIM + 1] = T(0.5) * (t1 - a);
+    w[DIM + 1] = halve(t1 - a);
 }
 
 // out[v] += sum_s R[v][s] w[s]
@@ -389,14 +458,15 @@ __device__ __forceinline__ double recon<double>(double a, double b, double c, do
     const double b0 = d0 * d0;
     const double b1 = d1 * d1;
     const double ed = e - d, ab = a - b;
-    const double t2 = ed - d0, s2 = fmaT(-2.0, d0, t2);
-    const double b2 = fmaT(13.0 / 12.0, t2 * t2, 0.25 * (s2 * s2));
-    const double t3 = ab + d1, s3 = fmaT(2.0, d1, t3);
-    const double b3 = fmaT(13.0 / 12.0, t3 * t3, 0.25 * (s3 * s3));
+    // (s / 2)^2 in place of s^2 / 4: the same bits, the halving off the FP64 pipe
+    const double t2 = ed - d0, s2 = halve(fmaT(-2.0, d0, t2));
+    const double b2 = fmaT(13.0 / 12.0, t2 * t2, s2 * s2);
+    const double t3 = ab + d1, s3 = halve(fmaT(2.0, d1, t3));
+    const double b3 = fmaT(13.0 / 12.0, t3 * t3, s3 * s3);
     const double te = d0 - d1;
     double t = fmaT(-2.0, te, t3) + t2;
-    double s = (ed - ab) - (d0 + d1);
-    const double tau = fmaT(13.0 / 12.0, t * t, 0.25 * (s * s));
+    double s = halve((ed - ab) - (d0 + d1));
+    const double tau = fmaT(13.0 / 12.0, t * t, s * s);
     double D0, D1, D2, D3, L01, L23;
     if (wmode == W_REG) {
         // Eq. eq18 (E_2 = E_3 = 0) and Eq. eq8-r

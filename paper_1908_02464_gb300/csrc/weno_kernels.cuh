@@ -104,8 +104,8 @@ struct SweepArgs {
     double lo0, dx0, lo1, dx1;   // x and y geometry (double Mach, jet)
     int stage;                   // RK stage (index of tm->xs_top)
     double xs_fixed;             // double Mach shock position when tm is null
-    // Primitives (cell_prims) of U's interior cells in U's layout, one plane
-    // of sv elements per entry.  P: read them (the first sweep of the stage
+    // Primitives (cell_prims) of U's interior cells: the record of the cell
+    // at index g of U's layout at P + PrimLayout::STRIDE g.  P: read them (the first sweep of the stage
     // wrote them); Pout: the tiles compute them and store those of their own
     // cells; both null: the tiles compute them and keep them to themselves.
     const void* P = nullptr;
@@ -199,7 +199,8 @@ __device__ __forceinline__ void stage_cell(const SweepArgs& a, const T* Ug, long
 // Fixed states compute theirs.
 template <typename T, int DIM, int DIR>
 __device__ __forceinline__ void stage_record(const SweepArgs& a, const T* Ug, const T* Pg, T* Pw, bool own,
-                                             long long line_base, int line, int along, int nd, T gamma, T* q)
+                                             long long line_base, int line, int along, int nd, T gamma, T gm1,
+                                             T* q)
 {
     constexpr int NV = DIM + 2;
     using PL = PrimLayout<DIM>;
@@ -210,19 +211,18 @@ __device__ __forceinline__ void stage_record(const SweepArgs& a, const T* Ug, co
     if (fixed >= 0) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) U[v] = pick<T>(a.bc_state[fixed][v], a.bc_state_f[fixed][v]);
-        cell_prepare<T, DIM, DIR>(U, gamma, q);
+        cell_prepare<T, DIM, DIR>(U, gamma, gm1, q);
         return;
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) U[v] = Ug[g + v * a.sv];
     if (Pg != nullptr) {
 #pragma unroll
-        for (int k = 0; k < PL::NP; ++k) P[k] = Pg[g + k * a.sv];
+        load_prims<DIM>(Pg, g, P);
     } else {
-        cell_prims<T, DIM>(U, gamma, P);
+        cell_prims<T, DIM>(U, gamma, gm1, P);
         if (Pw != nullptr && own) {
-#pragma unroll
-            for (int k = 0; k < PL::NP; ++k) Pw[g + k * a.sv] = P[k];
+            store_prims<DIM>(Pw, g, P);
         }
     }
     if (flip) {
@@ -332,6 +332,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
     const long long sl = DIR == 0 ? a.sy : 1LL;
     const long long sp = DIR == 2 ? a.sy : a.sz;
     const T gamma = pick<T>(a.gamma, a.gamma_f);
+    const T gm1 = gamma - T(1);
 
     const T* Ug = reinterpret_cast<const T*>(a.U);
 
@@ -391,7 +392,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
             int inplane;
             const long long base = flat_line(inA ? LA : LA + 1, inplane);
             T q[NQ];
-            stage_record<T, DIM, DIR>(a, Ug, Pg, Pw, own, base, inplane, inA ? fA0 + i : i, nd, gamma, q);
+            stage_record<T, DIM, DIR>(a, Ug, Pg, Pw, own, base, inplane, inA ? fA0 + i : i, nd, gamma, gm1, q);
             put(idx, q);
         }
     } else if (c0 >= 3 && c0 + SEG + 3 <= nd) {
@@ -408,13 +409,11 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
 #pragma unroll
                 for (int v = 0; v < NV; ++v) U[v] = Ug[g + v * a.sv];
                 if (Pg != nullptr) {
-#pragma unroll
-                    for (int k = 0; k < PrimLayout<DIM>::NP; ++k) P[k] = Pg[g + k * a.sv];
+                    load_prims<DIM>(Pg, g, P);
                 } else {
-                    cell_prims<T, DIM>(U, gamma, P);
+                    cell_prims<T, DIM>(U, gamma, gm1, P);
                     if (Pw != nullptr && p >= 3 && p < SEG + 3) {
-#pragma unroll
-                        for (int k = 0; k < PrimLayout<DIM>::NP; ++k) Pw[g + k * a.sv] = P[k];
+                        store_prims<DIM>(Pw, g, P);
                     }
                 }
                 cell_record<T, DIM, DIR>(U, P, q);
@@ -433,7 +432,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
                 const bool own = p >= 3 && p < SEG + 3 && along < nd;
                 T q[NQ];
                 stage_record<T, DIM, DIR>(a, Ug, Pg, Pw, own, a.off0 + (long long)line * sl + (long long)pb * sp,
-                                          line, along, nd, gamma, q);
+                                          line, along, nd, gamma, gm1, q);
                 put(idx, q);
             }
         }
@@ -470,7 +469,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
         if (valid) {
             auto ga = [&](int k) -> T { return cq[k * NCELL + cidx(l, p + 2)]; };
             auto gb = [&](int k) -> T { return cq[k * NCELL + cidx(l, p + 3)]; };
-            const Roe<T, DIM> r = roe_state<T, DIM>(ga, gb, gamma);
+            const Roe<T, DIM> r = roe_state<T, DIM>(ga, gb, gm1);
             // Eq. eq28 without the 1/60: w = L (U_{j-2} - 5U_{j-1} + 10U_j - 10U_{j+1} + 5U_{j+2} - U_{j+3})
             T dU[NV];
 #pragma unroll
@@ -545,9 +544,9 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
                 for (int s = 0; s < NV; ++s) fr[(FR::W + s) * NFACE + f] = w[s];
                 fr[FR::IRT2 * NFACE + f] = Ar<T>::rcp_f(r.rt * r.rt);
                 // half splitting speeds (Eq. flxuspliting: f+- = (g +- alpha v) / 2)
-                fr[FR::AM * NFACE + f] = T(0.5) * am;
-                fr[FR::A0 * NFACE + f] = T(0.5) * a0;
-                fr[FR::AP * NFACE + f] = T(0.5) * ap;
+                fr[FR::AM * NFACE + f] = halve(am);
+                fr[FR::A0 * NFACE + f] = halve(a0);
+                fr[FR::AP * NFACE + f] = halve(ap);
                 fr[FR::MASK * NFACE + f] = T(a.hybrid == 2 ? fmask : 0);
             }
             // a face is owned by the tile left of it, the last face by the last tile
@@ -619,7 +618,7 @@ __device__ __forceinline__ bool sweep_tile(const SweepArgs& a, int seg_blk, int 
 #pragma unroll
             for (int s = 0; s < NV; ++s) {
                 const T al = s == 0 ? am : (s == NV - 1 ? ap : a0);
-                const T h = T(0.5) * wg[s];
+                const T h = halve(wg[s]);
                 const T k = al * wv[s];   // al holds alpha / 2
                 // f+ in stencil order j-2 .. j+3, f- mirrored (j+3 .. j-2), so
                 // that both signs take the same call in 2b (neighbouring lanes
