@@ -38,3 +38,24 @@ def test_sweep_flops_formula():
     f = bench.sweep_flops(2, [10, 4], 0, 0)
     fc, fu, fw = bench.ALG_FLOPS[2]
     assert f == 40 * (fc + 8) + 44 * fu
+
+
+def test_direction_dependent_cell_flops():
+    """The per-cell operations a sweep that reads the stage's primitives is
+    credited with: the physical flux along the sweep (dim products u_n m_k,
+    the pressure sum, E + p and its product with u_n) and the two acoustic
+    eigenvalues u_n -+ c.  The rest of the oracle's cell count (velocity,
+    |u|^2, p, c, H) is at least what those primitives take."""
+    for dim in (1, 2, 3):
+        assert bench.ALG_FLOPS_CELL_DIR[dim] == dim + 1 + 2 + 2
+        prob = dict(dim=dim, n=[8] * dim, lo=[0] * dim, hi=[1] * dim, bc_lo=[0] * dim, bc_hi=[0] * dim)
+        U = np.array([1.0] + [0.3] * dim + [3.0])
+        c = orc.count_cell(prob, 0, U)
+        # primitives: dim divisions (velocity), one square root (c) and at
+        # least the dim products of |u|^2 remain outside the credited part
+        assert c.sum() - bench.ALG_FLOPS_CELL_DIR[dim] >= dim + 1 + dim
+        assert c[2] >= dim and c[3] == 1
+    assert bench.reads_prims("fp64", 2, 0) and not bench.reads_prims("fp64", 2, 1)
+    assert not bench.reads_prims("fp32", 2, 0) and not bench.reads_prims("fp64", 1, 0)
+    f = bench.sweep_flops(2, [10, 4], 0, 0, prims_read=True)
+    assert f == 40 * (bench.ALG_FLOPS_CELL_DIR[2] + 8) + 44 * bench.ALG_FLOPS[2][1]
