@@ -460,11 +460,13 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
             if (rec(m, CL::LP) > ap) { ap = rec(m, CL::LP); ip = m; }
         }
         T alb_m = T(0), alb_0 = T(0), alb_p = T(0);
-        T wb[NV];
+        T wb[NV], dUb[NV];
 #pragma unroll
-        for (int s = 0; s < NV; ++s) wb[s] = T(0);
+        for (int s = 0; s < NV; ++s) { wb[s] = T(0); dUb[s] = T(0); }
         if constexpr (PASS == 0) {
-            // F = [central(F) + R (alpha o w)] / 60; the gather applies the
+            // F = [central(F) + a0 dU + k0 R^{u-c} + k3 R^{u+c}] / 60 with
+            // k0 = (am - a0) w_0, k3 = (ap - a0) w_last, the form the forward
+            // sweep evaluates (ups_dissipation_add); the gather applies the
             // central weights to the bar Fb of the sum
             T Fb[NV];
 #pragma unroll
@@ -472,18 +474,35 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
                 Fb[v] = phi[v] * T(1.0 / 60.0);
                 UFf[CL::F + v] = Fb[v];
             }
-            T aw[NV], awb[NV];
-            aw[0] = am * w[0];
+            constexpr int LAST = NV - 1;
+            const T k0 = (am - a0) * w[0], k3 = (ap - a0) * w[LAST];
+            const T sum = k0 + k3, dd = k3 - k0;
+            const T unc = r.u[DIR] * r.c;
+            // out[0] += s; out[1 + k] += u_k s (+ c dd along DIR); out[E] += H s + u_n c dd
+            T sb = fmaT(r.H, Fb[LAST], Fb[0]);
 #pragma unroll
-            for (int s = 1; s < NV - 1; ++s) aw[s] = a0 * w[s];
-            aw[NV - 1] = ap * w[NV - 1];
-            back_proj_adj<T, DIM, DIR>(r, aw, Fb, awb, rb);
-            alb_m += awb[0] * w[0];
-            wb[0] += awb[0] * am;
+            for (int k = 0; k < DIM; ++k) {
+                sb = fmaT(r.u[k], Fb[1 + k], sb);
+                rb.u[k] = fmaT(sum, Fb[1 + k], rb.u[k]);
+            }
+            const T ddb = fmaT(r.c, Fb[1 + DIR], unc * Fb[LAST]);
+            rb.H = fmaT(sum, Fb[LAST], rb.H);
+            const T uncb = dd * Fb[LAST];
+            rb.u[DIR] = fmaT(uncb, r.c, rb.u[DIR]);
+            rb.c = fmaT(uncb, r.u[DIR], fmaT(dd, Fb[1 + DIR], rb.c));
+            const T k0b = sb - ddb, k3b = sb + ddb;
+            alb_m = k0b * w[0];
+            alb_p = k3b * w[LAST];
+            wb[0] = k0b * (am - a0);
+            wb[LAST] = k3b * (ap - a0);
+            // a0 dU: the entropy and shear fields' speed
+            T dot = T(0);
 #pragma unroll
-            for (int s = 1; s < NV - 1; ++s) { alb_0 += awb[s] * w[s]; wb[s] += awb[s] * a0; }
-            alb_p += awb[NV - 1] * w[NV - 1];
-            wb[NV - 1] += awb[NV - 1] * ap;
+            for (int v = 0; v < NV; ++v) {
+                dot = fmaT(Fb[v], dU[v], dot);
+                dUb[v] = a0 * Fb[v];
+            }
+            alb_0 = dot - alb_m - alb_p;
         } else {
             // projections of the six cells, all fields
             T vv[6][NV], gg[6][NV];
@@ -569,9 +588,6 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
             }
         }
         // detector: w = L dU, dU = (U0 - U5) + 5 (U4 - U1) + 10 (U2 - U3)
-        T dUb[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) dUb[v] = T(0);
         proj_all_adj<T, DIM, DIR>(r, dU, wb, dUb, rb);
         if constexpr (PASS == 0) {
 #pragma unroll
