@@ -41,7 +41,19 @@
 
 namespace wis {
 
-template <typename T> __device__ __forceinline__ T sgn(T x) { return x > T(0) ? T(1) : (x < T(0) ? T(-1) : T(0)); }
+// q sgn(x): q with x's sign applied, zero where x is zero; for double on the
+// integer pipes (the FP64 pipe bounds the adjoint), the same value as the
+// product for finite q (a zero result may differ in its sign only)
+__device__ __forceinline__ double times_sign(double q, double x)
+{
+    const long long xb = __double_as_longlong(x);
+    const long long r = __double_as_longlong(q) ^ (xb & (long long)0x8000000000000000ULL);
+    return (xb & 0x7fffffffffffffffLL) == 0 ? 0.0 : __longlong_as_double(r);
+}
+__device__ __forceinline__ float times_sign(float q, float x)
+{
+    return x > 0.0f ? q : (x < 0.0f ? -q : 0.0f);
+}
 
 // record bars of one cell (NQ entries, same layout as CellLayout) -> dU;
 // isq = 1/sqrt(rho) and ic = 1/c as cell_prepare computed them
@@ -66,10 +78,11 @@ __device__ __forceinline__ void cell_adj(const T* U, T gamma, T isq, T ic, const
 #pragma unroll
     for (int v = 0; v < NV; ++v) Ub[v] = qb[CL::U + v];
     T unb = T(0), cb = T(0), isqb = T(0), Epb = T(0), pb = T(0), irhob = T(0), m2b = T(0);
-    const T s1 = sgn(un - c), s0 = sgn(un), s2 = sgn(un + c);
-    unb += qb[CL::LM] * s1; cb -= qb[CL::LM] * s1;
-    unb += qb[CL::L0] * s0;
-    unb += qb[CL::LP] * s2; cb += qb[CL::LP] * s2;
+    // |un - c|, |un|, |un + c|: the bars take the signs of their arguments
+    const T lm = times_sign(qb[CL::LM], un - c), lp = times_sign(qb[CL::LP], un + c);
+    unb += lm; cb -= lm;
+    unb += times_sign(qb[CL::L0], un);
+    unb += lp; cb += lp;
     Ub[0] += qb[CL::SQ] * isq; isqb += qb[CL::SQ] * rho;
     Epb += qb[CL::SH] * isq; isqb += qb[CL::SH] * Ep;
 #pragma unroll
@@ -455,9 +468,12 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
         int im = 0, i0 = 0, ip = 0;
 #pragma unroll
         for (int m = 1; m < 6; ++m) {
-            if (rec(m, CL::LM) > am) { am = rec(m, CL::LM); im = m; }
-            if (rec(m, CL::L0) > a0) { a0 = rec(m, CL::L0); i0 = m; }
-            if (rec(m, CL::LP) > ap) { ap = rec(m, CL::LP); ip = m; }
+            // the speeds are non-negative: compared on their bit patterns
+            // (integer pipes), first index on ties as before
+            const T xm = rec(m, CL::LM), x0 = rec(m, CL::L0), xp = rec(m, CL::LP);
+            if (lt_nn(am, xm)) { am = xm; im = m; }
+            if (lt_nn(a0, x0)) { a0 = x0; i0 = m; }
+            if (lt_nn(ap, xp)) { ap = xp; ip = m; }
         }
         T alb_m = T(0), alb_0 = T(0), alb_p = T(0);
         T wb[NV], dUb[NV];
