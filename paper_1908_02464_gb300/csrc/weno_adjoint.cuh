@@ -94,15 +94,18 @@ __device__ __forceinline__ void cell_adj(const T* U, T gamma, T isq, T ic, const
     Ub[1 + DIR] += qb[CL::F + 0];
     Ub[DIM + 1] += Epb; pb += Epb;
     Ub[1 + DIR] += unb * irho; irhob += unb * U[1 + DIR];
-    // c = sqrt(gamma p irho)
-    const T cc = cb * T(0.5) * ic;
-    pb += cc * gamma * irho; irhob += cc * gamma * p;
+    // c = sqrt(gamma p irho): dc = gamma (irho dp + p dirho) / (2 c)
+    const T cg = halve(cb) * ic * gamma;
+    pb = fmaT(cg, irho, pb); irhob = fmaT(cg, p, irhob);
     // p = gm1 (E - irho m2 / 2)
-    Ub[DIM + 1] += pb * gm1; irhob -= pb * gm1 * T(0.5) * m2; m2b -= pb * gm1 * T(0.5) * irho;
+    const T pg = pb * gm1, hpg = halve(pg);
+    Ub[DIM + 1] += pg; irhob = fmaT(-hpg, m2, irhob); m2b = -hpg * irho;
+    // m2 = |m|^2, irho = isq^2, isq = rho^-1/2
+    const T m2b2 = m2b + m2b;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) Ub[1 + k] += T(2) * U[1 + k] * m2b;
-    isqb += T(2) * isq * irhob;
-    Ub[0] += isqb * (T(-0.5) * isq * irho);
+    for (int k = 0; k < DIM; ++k) Ub[1 + k] = fmaT(U[1 + k], m2b2, Ub[1 + k]);
+    isqb = fmaT(isq + isq, irhob, isqb);
+    Ub[0] = fmaT(isqb, -halve(isq) * irho, Ub[0]);
 }
 
 template <typename T, int DIM> struct RoeBar {
@@ -129,8 +132,8 @@ __device__ __forceinline__ void proj_all_adj(const Roe<T, DIM>& r, const T* x, c
     for (int k = 1; k < DIM; ++k) dot = fmaT(r.u[k], x[1 + k], dot);
     const T y = fmaT(r.hq2, x[0], x[DIM + 1]) - dot;
     const T z = fmaT(r.u[DIR], x[0], -x[1 + DIR]);
-    const T t1b = T(0.5) * wb[0] - wb[1] + T(0.5) * wb[LAST];
-    const T ab = T(0.5) * (wb[0] - wb[LAST]);
+    const T t1b = halve(wb[0] + wb[LAST]) - wb[1];
+    const T ab = halve(wb[0] - wb[LAST]);
     int s = 2;
 #pragma unroll
     for (int t = 0; t < DIM; ++t) {
@@ -199,9 +202,9 @@ __device__ __forceinline__ void roe_adj(GA get_a, GB get_b, T gamma, const Roe<T
     const T sa = get_a(CL::SQ), sb = get_b(CL::SQ);
     const T inv = Ar<T>::rcp_f(sa + sb);   // as in roe_state
     // b1 = gm1 ic^2; c = c2 ic (= sqrt c2); ic = c2^-1/2; c2 = gm1 (H - hq2)
-    rb.ic += rb.b1 * gm1 * T(2) * r.ic;
+    rb.ic = fmaT(rb.b1 * gm1, r.ic + r.ic, rb.ic);
     const T ic3 = r.ic * r.ic * r.ic;
-    const T c2b = rb.c * T(0.5) * r.ic - T(0.5) * rb.ic * ic3;
+    const T c2b = halve(fmaT(rb.c, r.ic, -rb.ic * ic3));
     rb.H += c2b * gm1;
     rb.hq2 -= c2b * gm1;
     T invb = T(0);
