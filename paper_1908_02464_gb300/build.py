@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libweno_is.so")
 UNITS = ["weno_api", "weno_f64", "weno_f32", "weno_mixed", "weno_noalloc", "weno_batch", "weno_batch2d"]
-HEADERS = ["weno_device.cuh", "weno_kernels.cuh", "weno_launch.cuh", "weno_adjoint.cuh", "weno_batch.cuh"]
+HEADERS = ["weno_device.cuh", "weno_kernels.cuh", "weno_march.cuh", "weno_launch.cuh", "weno_adjoint.cuh", "weno_batch.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -8,6 +8,7 @@
 
 #include "weno_adjoint.cuh"
 #include "weno_kernels.cuh"
+#include "weno_march.cuh"
 
 namespace wis {
 
@@ -31,7 +32,10 @@ namespace wis {
 //   6 flat256 the flat tile with 251 faces on 256 threads (two CTAs per SM):
 //             half the partly filled last warp per face, twice the WENO
 //             faces per tile; lines shorter than 250 cells take variant 3
-constexpr int kTileVariants = 7;
+//   7 march   float y and z sweeps: k_march, one lane per line marching
+//             along a 12-cell segment with the stencil in registers; float
+//             x sweeps take variant 3 and FP64 sweeps variant 5 instead
+constexpr int kTileVariants = 8;
 template <int V> struct Tile;
 template <> struct Tile<0> { static constexpr int LINES = 2, SEG = 63, NT = 128; static constexpr bool FLAT = false; };
 template <> struct Tile<1> { static constexpr int LINES = 8, SEG = 15, NT = 128; static constexpr bool FLAT = false; };
@@ -84,6 +88,13 @@ cudaError_t launch_sweep_v(int variant, const SweepArgs& a, cudaStream_t s)
     if (variant == 6) {
         if (a.n[DIR] >= Tile<6>::SEG) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<6>>(a, s);
         return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<3>>(a, s);
+    }
+    if (variant == 7) {
+        if constexpr (sizeof(T) == 4 && DIR >= 1) {
+            if (a.P == nullptr && a.Pout == nullptr) return launch_march<T, DIM, DIR, EXACTDET>(a, s);
+        }
+        if (sizeof(T) == 4) return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<3>>(a, s);
+        return launch_sweep_v<T, DIM, DIR, EXACTDET>(5, a, s);
     }
     return launch_sweep_one<T, DIM, DIR, EXACTDET, Tile<0>>(a, s);
 }

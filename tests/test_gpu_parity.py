@@ -508,17 +508,24 @@ def test_rhs_parity_3d_walls_flat_tiles():
     _compare_rhs(prob, U)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
 def test_tile_variants_give_bitwise_identical_results(precision):
     """Every face is computed by the same arithmetic whatever the tiling,
-    including flat tiles (variants 5 and 6) whose pieces span two lines, and
-    the fallback to variant 3 on lines shorter than 122 (250) cells."""
-    for prob, U in _variant_cases():
+    including flat tiles (variants 5 and 6) whose pieces span two lines, the
+    fallback to variant 3 on lines shorter than 122 (250) cells, and the
+    float marching sweeps across x (variant 7: segments of 12 cells, lines
+    of 9 to 263 cells, a ragged last warp of lines, every face on the WENO
+    path with the hybrid off)."""
+    cases = _variant_cases()
+    prob, U = P.random_state(2, [150, 37], seed=79, kind="mixed")
+    prob["hybrid"] = 0
+    cases.append((prob, U))
+    for prob, U in cases:
         if precision != "fp64" and prob["name"] == "mach2000_jet":
             continue   # FP32 cannot represent the jet's pressure (see the jet tests)
         dim = prob["dim"]
         outs = []
-        for v in range(7):
+        for v in range(8):
             s = weno.Solver(prob, precision)
             s.set_tiles([v] * dim)
             Ud = torch.from_numpy(U).cuda()
@@ -534,6 +541,30 @@ def test_tile_variants_give_bitwise_identical_results(precision):
             assert np.array_equal(outs[k], outs[k % 3]), (prob["name"], k // 3, k % 3)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_march_variant_equals_tiles_for_every_option(precision):
+    """The float marching sweeps across x (variant 7) against the 1x127 and
+    8x15 tiles (variants 3 and 1) under every weight rule, splitting and
+    hybrid mode, in 2D and 3D: right-hand side and face flags bitwise equal."""
+    opts = [dict(weights=w) for w in ("reg", "is", "wang", "linear")]
+    opts += [dict(splitting=sp) for sp in ("lf", "rf")]
+    opts += [dict(hybrid=2), dict(hybrid=0, splitting="rf")]
+    for dim, n in ((2, [70, 53]), (3, [33, 26, 14])):
+        for o in opts:
+            prob, U = P.random_state(dim, n, seed=81, kind="mixed")
+            prob.update(o)
+            outs = []
+            for v in (3, 1, 7):
+                s = weno.Solver(prob, precision)
+                s.set_tiles([v] * dim)
+                Ud = torch.from_numpy(U).cuda()
+                outs.append((s.rhs(Ud, 0.004).cpu().numpy(), s.face_flags(Ud, 0.004).cpu().numpy()))
+                s.close()
+            for r, f in outs[1:]:
+                assert np.array_equal(r, outs[0][0]), (dim, o)
+                assert np.array_equal(f, outs[0][1]), (dim, o)
+
+
 def test_autotune_keeps_state_and_results():
     prob, U = P.double_mach(256, 64)
     s = weno.Solver(prob, "fp64")
@@ -541,7 +572,7 @@ def test_autotune_keeps_state_and_results():
     s.advance(0.002)
     V0, t0 = s.get_state()
     v = s.autotune(2)
-    assert all(0 <= x < 7 for x in v)
+    assert all(0 <= x < 8 for x in v)
     V1, t1 = s.get_state()
     assert t1 == t0 and np.array_equal(V0, V1)
     s.close()
