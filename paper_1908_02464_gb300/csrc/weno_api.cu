@@ -62,6 +62,7 @@ struct weno_ctx {
     int tot_blocks = 1;
     int phase = 0;
     int tile[3] = {0, 0, 0};    // sweep tile variant per direction
+    bool x_first = false;       // sweep order of a stage: x .. last instead of last .. x
     double smax_floor = 0.0;    // CFL wave-speed sum of the fixed boundary states
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     bool graphs_ready = false;
@@ -143,12 +144,23 @@ static wis::SweepArgs sweep_args(weno_ctx* c, int dir)
     return a;
 }
 
-// the sweep at position i of a stage (directions from the last to x) reads
-// the accumulator of the sweeps before it: unscaled after the first one
-// (MODE_ACC_SET), scaled after an accumulating one
+// Direction of the sweep at position i of a stage.  The last sweep reads
+// the accumulator of the others and writes the stage's result (the RK
+// combination or the RHS), so it should be the kernel with the cheapest
+// epilogue on those extra accesses: the tiles along x, where they are
+// contiguous rows (directions from the last to x), or, when the float
+// marching sweep is the default across x, that sweep, whose lanes write
+// 128-byte rows in every direction and batch their loads (directions from x
+// to the last; 256^3 vortex FP32 RHS 1.59 -> 1.36 ms).  The order is fixed
+// when the context is created, so results do not depend on the tile shapes.
+static int sweep_dir(const weno_ctx* c, int i) { return c->x_first ? i : c->dim - 1 - i; }
+
+// the sweep at position i of a stage reads the accumulator of the sweeps
+// before it: unscaled after the first one (MODE_ACC_SET), scaled after an
+// accumulating one
 static void set_acc_scale(weno_ctx* c, wis::SweepArgs& a, int i)
 {
-    const double s = i == 1 ? c->inv_dx[c->dim - 1] * (1.0 / 60.0) : 1.0;
+    const double s = i == 1 ? c->inv_dx[sweep_dir(c, 0)] * (1.0 / 60.0) : 1.0;
     a.acc_scale = s;
     a.acc_scale_f = (float)s;
 }
@@ -205,18 +217,17 @@ static cudaError_t issue_stage(weno_ctx* c, void* in, const void* base, void* ou
         cudaError_t e = issue_lf(c, in, slot, c->tm, s);
         if (e != cudaSuccess) return e;
     }
-    // directions from the last to x: the sweep that fuses the RK update (and
-    // reads the accumulator and the base state, and writes the new state)
-    // runs along x, where those accesses are contiguous rows
+    // the last sweep (see sweep_dir) fuses the RK update: it reads the
+    // accumulator and the base state and writes the new state
     for (int i = 0; i < c->dim; ++i) {
-        const int d = c->dim - 1 - i;
+        const int d = sweep_dir(c, i);
         wis::SweepArgs a = sweep_args(c, d);
         set_acc_scale(c, a, i);
         a.U = in;
         a.tm = c->tm;
         a.stage = stage;
         a.alpha_g = c->alpha_g + slot * 9 + 3 * d;
-        if (d == 0) {
+        if (i == c->dim - 1) {
             a.mode = wis::MODE_COMBINE;
             a.Un = base;
             a.out = out;
@@ -484,6 +495,7 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
             const long long lanes = lines * ((ctx->n[d] + 11) / 12);
             if (lanes >= 4LL * ctx->nsm * 16 * 32) ctx->tile[d] = 7;
         }
+        ctx->x_first = dim >= 2 && ctx->tile[dim - 1] == 7;
     }
     if (dim == 1) ctx->tile[0] = 0;
     *out = ctx;
@@ -629,10 +641,10 @@ static weno_status issue_rhs(weno_ctx* ctx, const void* U, void* out, double t, 
         for (int k = 0; k < 3; ++k) nf *= (k == d - 1) ? (long long)ctx->n[k] + 1 : ctx->n[k];
         foff[d] = foff[d - 1] + nf;
     }
-    // directions from the last to x, as in a step: the sweep that writes the
-    // result runs along x
+    // the directions in the order of a step (sweep_dir): the last sweep
+    // writes the result
     for (int i = 0; i < ctx->dim; ++i) {
-        const int d = ctx->dim - 1 - i;
+        const int d = sweep_dir(ctx, i);
         wis::SweepArgs a = sweep_args(ctx, d);
         set_acc_scale(ctx, a, i);
         a.sy = sy; a.sz = sz; a.sv = sv; a.off0 = 0;
@@ -640,7 +652,7 @@ static weno_status issue_rhs(weno_ctx* ctx, const void* U, void* out, double t, 
         a.xs_fixed = wis::dmr_shock_x(t);
         a.alpha_g = ctx->alpha_g + 3 * 9 + 3 * d;
         if (flags) a.flags = flags + foff[d];
-        if (d == 0) {
+        if (i == ctx->dim - 1) {
             a.mode = wis::MODE_RHS;
             a.acc = ctx->dim > 1 ? ctx->acc : nullptr;
             a.out = out;

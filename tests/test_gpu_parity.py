@@ -627,6 +627,33 @@ def test_reduced_precision_rhs_close(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_reduced_precision_large_3d_grid_marching_sweeps(precision):
+    """256^3 vortex in float: the marching sweeps across x and the x-first
+    sweep order that large float grids take.  RHS against the FP64 RHS
+    within 1e-5 of the flux-term scale; two RK3 steps stay within 1e-5 of
+    the FP64 steps relative to the state."""
+    prob, U = P.vortex3d(256)
+    r64, f64 = _gpu_rhs(prob, U)
+    r32, f32 = _gpu_rhs(prob, U, precision)
+    T = parity_log.term_scale(prob, U)
+    err = np.max(np.abs(r32 - r64).reshape(5, -1), axis=1)
+    assert np.all(err <= 1e-5 * T), (err, T)
+    assert np.array_equal(f32, f64)
+    outs = {}
+    for prec in ("fp64", precision):
+        s = weno.Solver(prob, prec)
+        s.set_state(U)
+        s.advance(1.0, max_steps=2)
+        outs[prec] = s.get_state()[0].astype(np.float64)
+        s.close()
+    d = np.max(np.abs(outs[precision] - outs["fp64"]).reshape(5, -1), axis=1)
+    # per-variable scale; the momenta share one (w starts at zero)
+    sc = np.max(np.abs(outs["fp64"]).reshape(5, -1), axis=1)
+    sc[1:4] = np.max(sc[1:4])
+    assert np.all(d <= 1e-5 * sc), (d, sc)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
 def test_reduced_precision_sod_accuracy(precision):
     prob, U = P.sod(200)
     V, t, k = _run_gpu(prob, U, precision)
