@@ -185,6 +185,8 @@ __global__ void __launch_bounds__(WPB * 32, MINW / WPB) k_march(SweepArgs a)
             }
         }
     };
+    // each cell is loaded one step ahead of its use (two steps ahead: 256^3
+    // vortex RHS 2% slower)
     T Ucur[NV], Unx[NV];
     load_cell(0, Unx);
     {
