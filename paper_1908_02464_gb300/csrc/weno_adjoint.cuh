@@ -56,9 +56,10 @@ __device__ __forceinline__ float times_sign(float q, float x)
 }
 
 // record bars of one cell (NQ entries, same layout as CellLayout) -> dU;
-// isq = 1/sqrt(rho) and ic = 1/c as cell_prepare computed them
+// isq = 1/sqrt(rho), ic = 1/c, the pressure p and the sound speed c as
+// cell_prims computed them for the forward record
 template <typename T, int DIM, int DIR>
-__device__ __forceinline__ void cell_adj(const T* U, T gamma, T isq, T ic, const T* qb, T* Ub)
+__device__ __forceinline__ void cell_adj(const T* U, T gamma, T isq, T ic, T p, T c, const T* qb, T* Ub)
 {
     using CL = CellLayout<DIM>;
     constexpr int NV = DIM + 2;
@@ -69,9 +70,6 @@ __device__ __forceinline__ void cell_adj(const T* U, T gamma, T isq, T ic, const
 #pragma unroll
     for (int k = 0; k < DIM; ++k) m2 = fmaT(U[1 + k], U[1 + k], m2);
     const T E = U[DIM + 1];
-    const T p = gm1 * fmaT(T(-0.5) * irho, m2, E);
-    const T c2 = gamma * p * irho;
-    const T c = c2 * ic;   // as in the forward record
     const T un = U[1 + DIR] * irho;
     const T Ep = E + p;
 
@@ -315,6 +313,11 @@ struct VjpArgs {
     // while staging (the fields stage_cell reads: bc_lo, bc_hi, bc_state,
     // lo0, dx0, lo1, dx1, tm = null, xs_fixed)
     SweepArgs bc;
+    // cell primitives (cell_prims, PrimLayout records at STRIDE g): P read
+    // (an earlier direction stored them), Pout computed and stored for the
+    // tile's own cells, both null: computed and kept to the tile (FP64 only)
+    const void* P;
+    void* Pout;
 };
 
 // A tile is LINES grid lines x SEG cells along the sweep, one thread per
@@ -342,12 +345,16 @@ struct VjpSmem {
     // bars of cells 2 and 3 (the face's neighbours), the three LLF speed
     // bars, and (as one int) the stencil slots of the cells attaining the
     // speeds and whether the pass takes the face
+    // per cell after the record: 1/sqrt(rho), 1/c and, in FP64, p and c
+    // (in FP32 the per-cell reverse recomputes those two: two more staged
+    // rows cost the shared-memory-bound float tiles more than they save)
+    static constexpr int NX = sizeof(T) == 8 ? 4 : 2;
     static constexpr int NUF = 2 * NV;
     static constexpr int NUFF = PASS == 0 ? NUF : 6 * NUF;
     static constexpr int NRB = DIM + 2;
     static constexpr int NFB = NUFF + 2 * NRB + 3;
     static constexpr size_t bytes =
-        sizeof(T) * ((size_t)(NQ + 2) * LNC + (size_t)NV * LNC + (size_t)LNF * NFB) + sizeof(int) * (size_t)LNF;
+        sizeof(T) * ((size_t)(NQ + NX) * LNC + (size_t)NV * LNC + (size_t)LNF * NFB) + sizeof(int) * (size_t)LNF;
 };
 
 // Residency of the WENO pass: its per-face reverse needs more than 255
@@ -371,8 +378,8 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
     constexpr int LINES = SM::LINES, LNF = SM::LNF, LNC = SM::LNC;
     constexpr int NT = VjpTile<T, DIM, DIR>::NT;
     constexpr int NUF = SM::NUF, NUFF = SM::NUFF, NRB = SM::NRB;
-    T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ + 2][NC][LINES] cell records, 1/sqrt(rho), 1/c
-    T* wq = cq + (NQ + 2) * LNC;              // [NV][NC][LINES] cotangent
+    T* cq = reinterpret_cast<T*>(smem_raw);   // [NQ + NX][NC][LINES] records, 1/sqrt(rho), 1/c (, p, c)
+    T* wq = cq + (NQ + SM::NX) * LNC;         // [NV][NC][LINES] cotangent
     T* UF = wq + NV * LNC;                    // [NF][LINES][NUFF] U and F bars (see below)
     T* RB = UF + LNF * NUFF;                  // [NF][LINES][2][NRB] Roe-field bars of cells 2 and 3
     T* SP = RB + LNF * 2 * NRB;               // [NF][LINES][3] LLF speed bars
@@ -403,18 +410,55 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
             // in-plane index of the line for the boundary conditions: the row
             // for x sweeps, the column for y and z sweeps
             const int line = DIR == 0 ? j : ix0 + l;
-            T U[NV];
-            stage_cell<T, DIM, DIR>(a.bc, Ug, base0 + l, line, cell, nd, U);
+            using PL = PrimLayout<DIM>;
+            T U[NV], q[NQ], inv[2], P[PL::NP];
+            if constexpr (sizeof(T) == 8) {
+                long long gs = 0;
+                bool flip = false;
+                const int fixed = cell_source<DIR>(a.bc, base0 + l, line, cell, nd, gs, flip);
+                if (fixed >= 0) {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) U[v] = a.bc.bc_state[fixed][v];
+                    cell_prims<T, DIM>(U, gamma, gamma - T(1), P, inv);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) U[v] = Ug[gs + v * a.sv];
+                    if (a.P != nullptr) {
+                        // 1/sqrt(rho) = sqrt(rho) / rho and 1/c from the
+                        // stored record (within an ulp or two of the staged
+                        // values)
+                        load_prims<DIM>(reinterpret_cast<const T*>(a.P), gs, P);
+                        inv[0] = P[PL::SQ] * P[PL::IRHO];
+                        inv[1] = Ar<T>::rcp_f(P[PL::C]);
+                    } else {
+                        cell_prims<T, DIM>(U, gamma, gamma - T(1), P, inv);
+                        if (a.Pout != nullptr && cell >= c0 && cell < c0 + SEG && cell < nd)
+                            store_prims<DIM>(reinterpret_cast<T*>(a.Pout), gs, P);
+                    }
+                    if (flip) {
+                        U[1 + DIR] = -U[1 + DIR];
+                        P[PL::SU + DIR] = -P[PL::SU + DIR];
+                    }
+                }
+            } else {
+                // float: no stored primitives (the float tiles were measured
+                // slower with the source lookup above)
+                stage_cell<T, DIM, DIR>(a.bc, Ug, base0 + l, line, cell, nd, U);
+                cell_prims<T, DIM>(U, gamma, gamma - T(1), P, inv);
+            }
             const bool inside = cell >= 0 && cell < nd;
             const long long g = base0 + l + (long long)cell * sd;
 #pragma unroll
             for (int v = 0; v < NV; ++v) wq[v * LNC + idx] = inside ? Wg[g + v * a.sv] : T(0);
-            T q[NQ], inv[2];
-            cell_prepare<T, DIM, DIR>(U, gamma, gamma - T(1), q, inv);
+            cell_record<T, DIM, DIR>(U, P, q);
 #pragma unroll
             for (int kk = 0; kk < NQ; ++kk) cq[kk * LNC + idx] = q[kk];
             cq[NQ * LNC + idx] = inv[0];
             cq[(NQ + 1) * LNC + idx] = inv[1];
+            if constexpr (SM::NX == 4) {
+                cq[(NQ + 2) * LNC + idx] = P[PrimLayout<DIM>::P];
+                cq[(NQ + 3) * LNC + idx] = P[PrimLayout<DIM>::C];
+            }
         } else {
 #pragma unroll
             for (int v = 0; v < NV; ++v) wq[v * LNC + idx] = T(0);
@@ -643,7 +687,10 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
 #pragma unroll
         for (int kk = 0; kk < NQ; ++kk) qb[kk] = T(0);
         bool touched = false;
-        // central-flux and detector weights of stencil slot m
+        // pass 0 in FP64: the face (index into the face arrays) that gives
+        // this cell its stencil slot m, -1 where none does
+        int fslot[6] = {-1, -1, -1, -1, -1, -1};
+        // central-flux and detector weights of stencil slot m (pass 0 in FP32)
         constexpr T cf[6] = {T(1), T(-8), T(37), T(37), T(-8), T(1)};
         constexpr T cd[6] = {T(1), T(-5), T(10), T(-10), T(5), T(-1)};
 #pragma unroll
@@ -662,6 +709,8 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
                 const T* uf = UF + (size_t)ff * NUFF + m * NUF;
 #pragma unroll
                 for (int kk = 0; kk < NUF; ++kk) qb[kk] += uf[kk];
+            } else if constexpr (sizeof(T) == 8) {
+                fslot[m] = ff;
             } else {
                 const T* uf = UF + (size_t)ff * NUFF;
 #pragma unroll
@@ -679,12 +728,47 @@ __device__ __forceinline__ bool vjp_tile(const VjpArgs& a, int bx, int by, int b
             if (((sl >> 4) & 15) == m) qb[CL::L0] += SP[ff * 3 + 1];
             if (((sl >> 8) & 15) == m) qb[CL::LP] += SP[ff * 3 + 2];
         }
+        if constexpr (PASS == 0 && sizeof(T) == 8) {
+            // stencil weights of slot m: detector (1, -5, 10, -10, 5, -1)
+            // on the U slots, central flux (1, -8, 37, 37, -8, 1) on the F
+            // slots, applied as sums and differences of the symmetric pairs
+            // (10 FP64 operations per variable instead of 12; in FP32 the
+            // six loads held at once cost the 256-thread tiles a CTA per SM,
+            // so FP32 keeps one multiply-add per slot)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                T bu[6], bf[6];
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    const T* uf = UF + (size_t)(fslot[m] < 0 ? 0 : fslot[m]) * NUFF;
+                    bu[m] = fslot[m] < 0 ? T(0) : uf[CL::U + v];
+                    bf[m] = fslot[m] < 0 ? T(0) : uf[CL::F + v];
+                }
+                qb[CL::U + v] = fmaT(T(10), bu[2] - bu[3], fmaT(T(5), bu[4] - bu[1], bu[0] - bu[5]));
+                qb[CL::F + v] = fmaT(T(37), bf[2] + bf[3], fmaT(T(-8), bf[1] + bf[4], bf[0] + bf[5]));
+            }
+        }
         if (PASS == 1 && !touched) continue;
         const int pc = cell - (c0 - 5);
         T U[NV], Ub[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) U[v] = cq[(CL::U + v) * LNC + pc * LINES + l];
-        cell_adj<T, DIM, DIR>(U, gamma, cq[NQ * LNC + pc * LINES + l], cq[(NQ + 1) * LNC + pc * LINES + l], qb, Ub);
+        const int ci = pc * LINES + l;
+        const T isq = cq[NQ * LNC + ci], ic = cq[(NQ + 1) * LNC + ci];
+        T pc_p, pc_c;
+        if constexpr (SM::NX == 4) {
+            pc_p = cq[(NQ + 2) * LNC + ci];
+            pc_c = cq[(NQ + 3) * LNC + ci];
+        } else {
+            // p and c as cell_prims forms them
+            const T irho = isq * isq;
+            T m2 = T(0);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) m2 = fmaT(U[1 + k], U[1 + k], m2);
+            pc_p = (gamma - T(1)) * fmaT(T(-0.5) * irho, m2, U[DIM + 1]);
+            pc_c = gamma * pc_p * irho * ic;
+        }
+        cell_adj<T, DIM, DIR>(U, gamma, isq, ic, pc_p, pc_c, qb, Ub);
         if (owned) {
             const long long g = base0 + l + (long long)cell * sd;
 #pragma unroll

@@ -738,6 +738,15 @@ weno_status weno_rhs_vjp(weno_ctx* ctx, const void* U_dev, const void* w_dev, vo
         a.bc.sy = sy; a.bc.sz = sz; a.bc.sv = sv; a.bc.off0 = 0;
         a.bc.tm = nullptr;
         a.bc.xs_fixed = wis::dmr_shock_x(t);
+        // FP64: the x pass computes the cell primitives of U and stores
+        // them, the y and z passes read them (as the forward sweeps share
+        // theirs within a stage)
+        a.P = nullptr;
+        a.Pout = nullptr;
+        if (ctx->use_prims) {
+            if (d == 0) a.Pout = ctx->prim;
+            else a.P = ctx->prim;
+        }
         CK(f64 ? wis::vjp_f64(ctx->dim, d, a, ctx->stream) : wis::vjp_f32(ctx->dim, d, a, ctx->stream));
         wis::GhostArgs ga = ghost_args(ctx, gU_dev, d);
         ga.sy = sy; ga.sz = sz; ga.sv = sv; ga.off0 = 0;
