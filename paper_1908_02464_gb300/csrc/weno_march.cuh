@@ -402,9 +402,10 @@ __global__ void __launch_bounds__(WPB * 32, MINW / WPB) k_march(SweepArgs a)
 
 // Launch of k_march: segments of 12 cells, two warps per CTA.  A segment
 // stages 18 cells for its 13 faces (the first face is also the previous
-// segment's last); 12 cells give 16 resident warps per SM enough lanes on
-// grids of a few million cells, longer segments would need more shared
-// memory per warp for the face fluxes.
+// segment's last); 12-cell segments give the 12 (3D) or 16 (2D) resident
+// warps per SM several rounds of lanes on grids of a few million cells,
+// longer segments would need more shared memory per warp for the face
+// fluxes.
 template <typename T, int DIM, int DIR, bool EXACTDET>
 cudaError_t launch_march(const SweepArgs& a, cudaStream_t s)
 {
