@@ -216,10 +216,11 @@ weno_status weno_time_sweeps(weno_ctx* ctx, int reps, void* flush_dev, size_t fl
  * start the next; lines shorter than 122 cells take variant 3), 6: flat
  * with 251 faces on 256 threads (lines shorter than 250 take 3), 7: FP32
  * and mixed sweeps across x (y, z) by marching warps, one lane per line
- * along a 12-cell segment with the six-cell stencil in registers (FP32
- * along x takes 3, FP64 takes 5).  Defaults: FP64 5 in every direction
- * except along y in 3D (2); FP32 and mixed 3 along x, 1 across, 7 across
- * when lines x segments reach four rounds of 16 warps on every SM.
+ * along a segment of 12 (2D) or 18 (3D) cells with the six-cell stencil
+ * in registers (FP32 along x takes 3, FP64 takes 5).  Defaults: FP64 5 in
+ * every direction except along y in 3D (2); FP32 and mixed 3 along x, 1
+ * across, 7 across when lines x segments reach four rounds of 16 warps on
+ * every SM.
  * variants[3] (if not NULL) receives the choice per direction.
  * The state is not changed; the step graphs are rebuilt on next use.
  * Synchronizes. */

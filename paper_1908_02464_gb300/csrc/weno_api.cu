@@ -483,8 +483,8 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
     // FP64: flat tiles, except along y in 3D, where 4 x-adjacent lines per
     // tile share the 32-byte sectors of the strided loads (256^3 RHS 18.4
     // -> 17.3 ms); FP32 and mixed: 1 x 127 along x, 8 x 15 across, and the
-    // marching sweep (variant 7) across x when its lanes (lines x 12-cell
-    // segments) fill at least four rounds of 16 warps per SM: on the 256^3
+    // marching sweep (variant 7) across x when its lanes (lines x segments)
+    // fill at least four rounds of 16 warps per SM: on the 256^3
     // vortex it runs the RHS in 1.72 ms against 2.07, on the 2048 x 512
     // double Mach reflection (0.3 rounds) its y-sweep takes 3x the tiles' time
     for (int d = 0; d < dim; ++d)
@@ -492,7 +492,8 @@ weno_status weno_create(const weno_grid* grid, const weno_params* params, void* 
     if (ctx->prec != WENO_FP64) {
         for (int d = 1; d < dim; ++d) {
             const long long lines = (long long)ctx->n[0] * (d == 1 ? ctx->n[2] : ctx->n[1]);
-            const long long lanes = lines * ((ctx->n[d] + 11) / 12);
+            const int seg = dim == 3 ? wis::kMarchSeg3 : wis::kMarchSeg2;
+            const long long lanes = lines * ((ctx->n[d] + seg - 1) / seg);
             if (lanes >= 4LL * ctx->nsm * 16 * 32) ctx->tile[d] = 7;
         }
         ctx->x_first = dim >= 2 && ctx->tile[dim - 1] == 7;

@@ -33,8 +33,9 @@ namespace wis {
 //             half the partly filled last warp per face, twice the WENO
 //             faces per tile; lines shorter than 250 cells take variant 3
 //   7 march   float y and z sweeps: k_march, one lane per line marching
-//             along a 12-cell segment with the stencil in registers; float
-//             x sweeps take variant 3 and FP64 sweeps variant 5 instead
+//             along a segment (12 cells in 2D, 18 in 3D) with the stencil in
+//             registers; float x sweeps take variant 3 and FP64 sweeps
+//             variant 5 instead
 constexpr int kTileVariants = 8;
 template <int V> struct Tile;
 template <> struct Tile<0> { static constexpr int LINES = 2, SEG = 63, NT = 128; static constexpr bool FLAT = false; };

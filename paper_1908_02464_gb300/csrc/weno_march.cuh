@@ -22,6 +22,10 @@
 
 namespace wis {
 
+// cells per marching segment in 2D and 3D (the default tile rule of the host
+// code counts lanes with them)
+constexpr int kMarchSeg2 = 12, kMarchSeg3 = 18;
+
 // Shared memory of one warp: the face fluxes of its 32 segments, its list of
 // WENO faces and the buffers of one round of QW WENO faces.
 template <typename T, int DIM, int S>
@@ -30,7 +34,7 @@ struct MarchSmem {
     static constexpr int NQ = CellLayout<DIM>::NQ;
     static constexpr int NR = FaceRec<T, DIM>::NR;
     static constexpr int NF = S + 1;                  // faces of a segment of S cells
-    static constexpr int QW = DIM == 2 ? 8 : 6;       // WENO faces per round
+    static constexpr int QW = DIM == 2 ? 8 : (S > 12 ? 4 : 6);   // WENO faces per round
     static constexpr int FB = NV * NF * 32;           // [NV][NF][lane] face fluxes (x60)
     static constexpr int CR = QW * 6 * NQ;            // [QW][6][NQ] stencil cell records
     static constexpr int FRC = NR * QW;               // [NR][QW] WENO face records
@@ -400,16 +404,17 @@ __global__ void __launch_bounds__(WPB * 32, MINW / WPB) k_march(SweepArgs a)
     if (bad) atomicOr(&a.tm->status, 1);
 }
 
-// Launch of k_march: segments of 12 cells, two warps per CTA.  A segment
-// stages 18 cells for its 13 faces (the first face is also the previous
-// segment's last); 12-cell segments give the 12 (3D) or 16 (2D) resident
-// warps per SM several rounds of lanes on grids of a few million cells,
-// longer segments would need more shared memory per warp for the face
-// fluxes.
+// Launch of k_march: segments of 12 cells in 2D and 18 in 3D, two warps per
+// CTA.  A segment stages S + 6 cells for its S + 1 faces (the first face is
+// also the previous segment's last).  In 3D the 18-cell segments (24 records
+// for 19 faces) ran the 256^3 vortex y- and z-sweeps in 0.341 ms against
+// 0.367 ms with 12 cells, with 4 WENO faces per round so that 6 CTAs (12
+// warps) still fit in shared memory; in 2D 12-cell segments keep 16 warps
+// per SM.
 template <typename T, int DIM, int DIR, bool EXACTDET>
 cudaError_t launch_march(const SweepArgs& a, cudaStream_t s)
 {
-    constexpr int S = 12, WPB = 2;
+    constexpr int S = DIM == 3 ? kMarchSeg3 : kMarchSeg2, WPB = 2;
     using MS = MarchSmem<T, DIM, S>;
     // 3D: 12 resident warps per SM leave 160 registers a thread and no
     // spills (256^3 vortex RHS 1.68 -> 1.59 ms against 16 warps at 128
